@@ -1,0 +1,387 @@
+"""Benchmark of the Fastfood feature map on GB300 (one JSON line on rank 0).
+
+Workload (per GPU): N = 60000 MNIST-shaped rows (784 values, ~80% zeros,
+others U[0,1), padded to d = 1024), E = 16 RBF expansions, sigma = 3,
+Philox seed 42. One step = one fused feature pass over the batch:
+60000 x 32768 float32 features (7.9 GB) written to HBM. Inputs (188 MB) and
+outputs (7.9 GB) are larger than the 129 MB L2, so no flush is needed.
+
+Reported:
+  value      features/s of the whole job (all ranks), device-resident inputs
+  e2e        the same metric through the C ABI with pinned host buffers, the
+             host->device input copy and device->host feature copy inside
+             the timed region
+  roofline   the feature kernel's algorithmic bytes (784*4 read + 32768*4
+             written per row) / its CUDA-event time, against the measured
+             HBM copy bandwidth
+  train_step config 3 (N=512, E=16, 10 classes): fused forward + adjoint
+             backward vs the plain path (materialised features + torch linear
+             + torch cross-entropy + adjoint from dphi), both at equal accuracy
+  fused_logits softmax-ready logits of the same 60000-row batch without
+             writing features
+  cpu_baseline the FP64 oracle on a bounded sample of the same workload
+
+--impl reference times the oracle itself (CPU) on the same workload, as the
+reference arm.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+D, E, N, IN_DIM, SIGMA, SEED, C = 1024, 16, 60000, 784, 3.0, 42, 10
+F = 2 * E * D
+METRIC = "Fastfood features/sec at d=1024,E=16 (MNIST-shaped, 784 padded to 1024)"
+WORKLOAD = {"workload": "fastfood_features_rbf", "d": D, "E": E, "in_dim": IN_DIM,
+            "batch_per_gpu": N, "sigma": SIGMA, "seed": SEED,
+            "l2": "inputs (188 MB) and outputs (7.9 GB) larger than L2; no flush"}
+CPU_SAMPLE_ROWS = 1536
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--no-extras", action="store_true", help="skip train_step/fused_logits/e2e/cpu legs")
+    return p.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("features.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1702_08159_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """Per-launch DRAM bytes from the committed ncu summary, if the kernel is unchanged."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            j = json.load(f)
+        e = j.get(kernel)
+        if e and e.get("source_hash") == kernel_source_hash():
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            f = [s.strip() for s in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(rows=CPU_SAMPLE_ROWS):
+    """The FP64 oracle (as it stands, single thread) on `rows` rows of the workload."""
+    import workloads as wl
+    from oracle import fastfood as ff
+
+    T = ff.plan_tables(D, E, ff.RBF, SIGMA, seed=SEED)
+    x = wl.mnist_like(rows, IN_DIM, seed=SEED).astype(np.float64)
+    t0 = time.perf_counter()
+    ff.features(x, T)
+    dt = time.perf_counter() - t0
+    return {"value": rows * F / dt, "unit": "features/s", "cores": 1, "kind": "oracle",
+            "sample": f"{rows} rows of the workload (d={D}, E={E}), float64 numpy, {dt:.1f} s"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import workloads as wl
+    from oracle import fastfood as ff
+
+    T = ff.plan_tables(D, E, ff.RBF, SIGMA, seed=SEED)
+    rows = 256
+    x = wl.mnist_like(rows, IN_DIM, seed=SEED).astype(np.float64)
+    for _ in range(args.warmup):
+        ff.features(x[:16], T)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ff.features(x, T)
+    dt = time.perf_counter() - t0
+    v = rows * F * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "features/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, reference_step_rows=rows),
+            "cpu_baseline": {"value": v, "unit": "features/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{rows} rows per step, float64 numpy oracle"},
+            "e2e": {"value": v, "unit": "features/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    import paper_1702_08159_gb300 as mck
+    import workloads as wl
+    from paper_1702_08159_gb300 import build, dist as mdist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    build.build()
+
+    plan = mck.Plan(D, E, "rbf", SIGMA, SEED)
+    x_host = wl.mnist_like(N, IN_DIM, seed=SEED + rank)
+    x = torch.from_numpy(x_host).to(dev)
+    phi = torch.empty((N, F), device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier(device_ids=[local])
+
+    for _ in range(args.warmup):
+        mck.features(plan, x, out=phi)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            mck.features(plan, x, out=phi)
+            ev[i][1].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms_local = t_start.elapsed_time(t_end)
+    ms = mdist.max_over_ranks(ms_local, device=dev)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    avg_launch_s = statistics.mean(launch_ms) / 1e3
+    value = world * N * F * args.steps / (ms / 1e3)
+
+    bytes_per_row = IN_DIM * 4 + F * 4
+    peak, peak_kind = measured_peaks()
+    achieved = N * bytes_per_row / avg_launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                "kernel": "k_feat_warp<10,0>", "bytes_per_launch": N * bytes_per_row,
+                "traffic": ncu_traffic("k_feat_warp<10,0>")}
+
+    line = {"metric": METRIC, "value": value, "unit": "features/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (MNIST-shaped stand-in, seeded)",
+            "config": dict(WORKLOAD, parallelism=f"dp{world} (samples sharded, no collective)"),
+            "hbm_gbs": world * N * bytes_per_row * args.steps / (ms / 1e3) / 1e9,
+            "roofline": roofline, "clocks": clk.summary(), "gpu_launches": args.steps,
+            "launch_ms": {"mean": statistics.mean(launch_ms), "min": min(launch_ms),
+                          "max": max(launch_ms)}}
+
+    if not args.no_extras:
+        line["e2e"] = e2e_leg(mck, plan, x_host, dev, stream, world)
+        line["fused_logits"] = fused_logits_leg(mck, plan, x, dev, stream, args)
+        line["train_step"] = train_step_leg(mck, dev, stream, args)
+    del phi
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["cpu_baseline"] = cpu_baseline()
+    elif rank == 0:
+        line["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def e2e_leg(mck, plan, x_host, dev, stream, world):
+    """features/s through the public API with pinned host input and output."""
+    import torch
+
+    from paper_1702_08159_gb300 import dist as mdist
+
+    steps = 3
+    xin = torch.from_numpy(x_host).pin_memory()
+    out_host = torch.empty((N, F), dtype=torch.float32, pin_memory=True)
+    xd = torch.empty((N, IN_DIM), device=dev)
+    phi = torch.empty((N, F), device=dev)
+
+    def step():
+        xd.copy_(xin, non_blocking=True)
+        mck.features(plan, xd, out=phi)
+        out_host.copy_(phi, non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = mdist.max_over_ranks(a.elapsed_time(b), device=dev)
+    del out_host, phi
+    return {"value": world * N * F * steps / (ms / 1e3), "unit": "features/s",
+            "h2d_bytes_per_step": N * IN_DIM * 4, "d2h_bytes_per_step": N * F * 4,
+            "steps": steps, "ms_per_step": ms / steps}
+
+
+def fused_logits_leg(mck, plan, x, dev, stream, args):
+    import torch
+
+    import workloads as wl
+
+    W, b = wl.logit_weights(C, F, seed=SEED)
+    Wd, bd = torch.from_numpy(W).to(dev), torch.from_numpy(b).to(dev)
+    out = torch.empty((N, C), device=dev)
+    for _ in range(2):
+        mck.fused_logits(plan, x, Wd, bd, out=out)
+    torch.cuda.synchronize()
+    steps = max(3, args.steps // 4)
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        mck.fused_logits(plan, x, Wd, bd, out=out)
+    e.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(e) / steps
+    # FP32 FMAs: features' transforms are not counted; the contraction is C*2Ed per row.
+    return {"samples_per_s": N / (ms / 1e3), "features_per_s": N * F / (ms / 1e3),
+            "ms_per_call": ms, "num_classes": C, "gpu_launches_per_call": 2}
+
+
+def train_step_leg(mck, dev, stream, args):
+    """Config 3: N=512, d=1024, E=16, 10 classes; fused vs plain fwd+bwd step time."""
+    import torch
+
+    import workloads as wl
+    from paper_1702_08159_gb300.autograd import FastfoodFeatures, McKernelClassifier
+
+    n = 512
+    plan = mck.Plan(D, E, "rbf", 1.0, SEED)
+    x = torch.from_numpy(wl.mnist_like(n, IN_DIM, seed=SEED)).to(dev)
+    y = torch.from_numpy(wl.labels(n, C, seed=SEED)).to(dev)
+    W, b = wl.logit_weights(C, F, seed=SEED)
+    model = McKernelClassifier(plan, C, torch.from_numpy(W), torch.from_numpy(b))
+    Cs = model.Cs.detach().clone().requires_grad_(True)
+    G = model.G.detach().clone().requires_grad_(True)
+    Wp = model.W.detach().clone().requires_grad_(True)
+    bp = model.b.detach().clone().requires_grad_(True)
+
+    def fused():
+        for p in model.parameters():
+            p.grad = None
+        model.loss(x, y).backward()
+
+    def plain():
+        for p in (Cs, G, Wp, bp):
+            p.grad = None
+        phi = FastfoodFeatures.apply(plan, x, Cs, G)
+        loss = torch.nn.functional.cross_entropy(phi @ Wp.T + bp, y.long())
+        loss.backward()
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        steps = max(5, args.steps)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        e.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(e) / steps
+
+    tf, tp = timed(fused), timed(plain)
+    # equal accuracy: the two paths' gradients agree
+    fused()
+    plain()
+    torch.cuda.synchronize()
+    dmax = max(float((model.W.grad - Wp.grad).abs().max() / Wp.grad.abs().max()),
+               float((model.G.grad - G.grad).abs().max() / G.grad.abs().max()))
+    plan.close()
+    return {"batch": n, "ms_fused": tf, "ms_plain": tp, "speedup_vs_plain": tp / tf,
+            "grad_rel_diff_fused_vs_plain": dmax,
+            "plain": "mck_features + torch matmul + torch cross_entropy + mck_features_backward"}
+
+
+if __name__ == "__main__":
+    main()

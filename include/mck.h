@@ -1,0 +1,179 @@
+/*
+ * mck.h -- C ABI of the GB300 McKernel / Fastfood feature-map library (libmck.so).
+ *
+ * The library computes the random-feature map of McKernel (arXiv 1702.08159):
+ *
+ *   Z-hat = (1/(sigma sqrt d)) C H G Pi H B                      (Eq. etn:mckernel)
+ *   phi(x) = [cos(Z-hat x-hat), sin(Z-hat x-hat)] per expansion  (Eq. etn:mcfeatures)
+ *
+ * with x-hat = x zero-padded to d = 2^L (Fig. 1 caption), E independent
+ * expansions (Sec. "McKernel": "generate multiple instances of Z-hat"), and
+ * the classifier softmax(W phi + b) of Sec. "Empirical Analysis and
+ * Experiments". B (signs), Pi (permutation), G (Gaussian) and the calibration
+ * C are recreated from a seed by a counter-based hash (Sec. "API
+ * Description": parameters are deterministic functions of a hash, nothing is
+ * stored).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All array arguments are DEVICE pointers (CUDA global memory on the plan's
+ *   device), owned by the caller; the library never frees or retains them.
+ *   The only exception is mck_plan_tables, which fills HOST buffers.
+ * - Arrays are dense row-major float32 (int32 for labels). The feature row
+ *   of one sample holds E blocks of [cos (d values) | sin (d values)], so a
+ *   feature matrix is n x (2 E d) with leading dimension 2 E d.
+ * - x is n x in_dim with leading dimension ldx >= in_dim (elements).
+ * - Cs is the calibration already scaled by 1/(sigma sqrt d): Cs = C/(sigma sqrt d),
+ *   E x d. G is E x d. Passing NULL for Cs or G uses the plan's own tables;
+ *   passing arrays lets training code learn them (Sec. "Empirical Analysis":
+ *   learning C and G by backpropagation).
+ * - `stream` is a cudaStream_t (NULL = the legacy default stream). Every
+ *   compute call is asynchronous on that stream; the library may allocate
+ *   stream-ordered scratch memory (cudaMallocAsync) on it.
+ * - Gradients are written (not accumulated). Reductions over the batch (dCs,
+ *   dG, dW, db) are deterministic: the same inputs give bit-identical outputs.
+ * - Every call returns an mck_status_t. On failure mck_last_error() gives a
+ *   message for the calling thread. Argument errors are detected before any
+ *   device work is queued. MCK_ECUDA reports a CUDA runtime error.
+ * - Sizes: 2 <= d <= 2^15 for plans; n >= 0 (n = 0 is a no-op).
+ */
+#ifndef MCK_H
+#define MCK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mck_plan_s* mck_plan_t; /* opaque; owns the device tables of one parameter set */
+typedef void* mck_stream_t;            /* a cudaStream_t */
+
+typedef enum {
+  MCK_RBF = 0,    /* Gaussian RBF kernel exp(-|x-x'|^2/(2 sigma^2)) (Eq. etn:rbf) */
+  MCK_MATERN = 1  /* RBF Matern: C_kk = |sum of t uniform unit-ball points| (Sec. "Customizing McKernel") */
+} mck_kernel_t;
+
+typedef enum {
+  MCK_OK = 0,
+  MCK_EINVAL = -1,       /* an argument is out of range, NULL or misaligned */
+  MCK_ENOMEM = -2,       /* a device or host allocation failed */
+  MCK_ECUDA = -3,        /* the CUDA runtime reported an error */
+  MCK_ETIMEOUT = -4,     /* a bounded device wait gave up */
+  MCK_EUNSUPPORTED = -5  /* valid request this version does not implement */
+} mck_status_t;
+
+typedef enum {
+  MCK_FP32 = 0  /* the transform in float32 arithmetic */
+} mck_prec_t;
+
+#define MCK_MAX_LOG2_D 15          /* largest plan dimension: d = 2^15 */
+#define MCK_MAX_LOG2_D_FWHT 20     /* largest standalone transform: d = 2^20 */
+#define MCK_MAX_CLASSES 16         /* largest class count of the fused logit kernels */
+
+/* Create a plan: the tables B, Pi, G and C of E expansions of dimension d,
+ * recreated from `seed` (Sec. "McKernel" items B, Pi, G, C; Sec. "API
+ * Description": factory pattern, parameters from a hash).
+ *   d       padded dimension, a power of two, 2 <= d <= 2^15
+ *   E       number of expansions, 1 <= E <= 65536
+ *   kernel  MCK_RBF or MCK_MATERN
+ *   sigma   kernel width, finite and > 0 (the sigma of Eq. etn:mckernel)
+ *   seed    64-bit hash key; equal seeds give bit-identical B and Pi
+ * The Matern order t defaults to 40 (the paper's experiments, Fig. 2-4
+ * captions). The plan is created on the current CUDA device. The call is
+ * synchronous: the tables are ready when it returns. *out is set only on
+ * success. Errors: MCK_EINVAL (bad argument, NULL out), MCK_EUNSUPPORTED
+ * (d > 2^15), MCK_ENOMEM, MCK_ECUDA. */
+mck_status_t mck_plan(mck_plan_t* out, int64_t d, int32_t E, int32_t kernel, double sigma,
+                      uint64_t seed);
+
+/* As mck_plan, with the Matern order t (1 <= t <= 4096; ignored for RBF) and
+ * the CUDA device index (-1 = current device). */
+mck_status_t mck_plan_ex(mck_plan_t* out, int64_t d, int32_t E, int32_t kernel, double sigma,
+                         int32_t matern_t, uint64_t seed, int32_t device);
+
+/* Release a plan and its device tables (synchronises the device first so no
+ * queued call still reads them). NULL is ignored. */
+void mck_plan_destroy(mck_plan_t plan);
+
+/* Report the parameters of a plan; any output pointer may be NULL. */
+mck_status_t mck_plan_info(mck_plan_t plan, int64_t* d, int32_t* E, int32_t* kernel,
+                           double* sigma, int32_t* matern_t, uint64_t* seed, int32_t* device);
+
+/* Copy the plan's tables to HOST buffers (any may be NULL); synchronous.
+ *   B_bits  E x ceil(d/32) uint32: bit (k mod 32) of word k/32 is 1 where B_e[k] = -1
+ *   perm    E x d uint32: pi_e(k), with (Pi v)_k = v_{pi(k)} (Sec. "McKernel", Pi)
+ *   G       E x d float32 (Sec. "McKernel", G)
+ *   Cs      E x d float32: C/(sigma sqrt d) (Eq. etn:mckernel) */
+mck_status_t mck_plan_tables(mck_plan_t plan, uint32_t* B_bits, uint32_t* perm, float* G,
+                             float* Cs);
+
+/* In-place unnormalised Walsh-Hadamard transform of n vectors of length d
+ * (Sec. "Fast Walsh Hadamard": H_n = [[H_{n-1}, H_{n-1}], [H_{n-1}, -H_{n-1}]]).
+ *   x     device, n x d float32, contiguous, 16-byte aligned when d >= 4
+ *   n     number of vectors (>= 0)
+ *   d     power of two, 1 <= d <= 2^20
+ *   prec  MCK_FP32
+ * d <= 2^15 runs one pass over HBM; larger d runs two. */
+mck_status_t mck_fwht(float* x, int64_t n, int64_t d, int32_t prec, mck_stream_t stream);
+
+/* phi = features of n samples (Eq. etn:mckernel, Eq. etn:mcfeatures).
+ *   x       device n x in_dim (ld ldx), 1 <= in_dim <= d; padded with zeros to d
+ *   Cs, G   device E x d or NULL (plan tables)
+ *   phi     device n x (2 E d), 16-byte aligned; row = E blocks of [cos | sin] */
+mck_status_t mck_features(mck_plan_t plan, const float* x, int64_t n, int64_t in_dim,
+                          int64_t ldx, const float* Cs, const float* G, float* phi,
+                          mck_stream_t stream);
+
+/* Gradients of sum(phi(x) * dphi) (the adjoint of mck_features, with H^T = H
+ * and Pi^T = Pi^{-1}; the forward is recomputed, nothing is stored).
+ *   dphi  device n x (2 E d)
+ *   dx    device n x in_dim (ld ldx) or NULL
+ *   dCs   device E x d or NULL: sum over samples of h * dz
+ *   dG    device E x d or NULL: sum over samples of v * dw
+ * Uses stream-ordered scratch memory of about 2 E d x 4 bytes per 8 samples. */
+mck_status_t mck_features_backward(mck_plan_t plan, const float* x, int64_t n, int64_t in_dim,
+                                   int64_t ldx, const float* Cs, const float* G,
+                                   const float* dphi, float* dx, float* dCs, float* dG,
+                                   mck_stream_t stream);
+
+/* logits = phi(x) W^T + b without writing phi to memory (Sec. "Empirical
+ * Analysis": softmax(W phi + b); the softmax itself is mck_softmax_xent).
+ *   W        device num_classes x (2 E d)
+ *   b        device num_classes or NULL (zero bias)
+ *   logits   device n x num_classes
+ * 1 <= num_classes <= MCK_MAX_CLASSES. Uses stream-ordered scratch memory of
+ * n x E x num_classes floats. */
+mck_status_t mck_fused_logits(mck_plan_t plan, const float* x, int64_t n, int64_t in_dim,
+                              int64_t ldx, const float* Cs, const float* G, const float* W,
+                              const float* b, int32_t num_classes, float* logits,
+                              mck_stream_t stream);
+
+/* Gradients of sum(logits * dlogits) for mck_fused_logits: dx, dCs, dG, dW
+ * (num_classes x 2Ed) and db (num_classes); any output may be NULL. */
+mck_status_t mck_fused_logits_backward(mck_plan_t plan, const float* x, int64_t n,
+                                       int64_t in_dim, int64_t ldx, const float* Cs,
+                                       const float* G, const float* W, int32_t num_classes,
+                                       const float* dlogits, float* dx, float* dCs, float* dG,
+                                       float* dW, float* db, mck_stream_t stream);
+
+/* Mean softmax cross-entropy of logits (n x num_classes) against labels
+ * (int32 in [0, num_classes)), the multi-class form of the logistic loss of
+ * Eq. etn:loss. loss: device float[1] or NULL; dlogits: device n x
+ * num_classes or NULL, (softmax - onehot)/n. A label outside the range makes
+ * that row contribute 0 to loss and dlogits (a non-fatal data error). */
+mck_status_t mck_softmax_xent(const float* logits, const int32_t* labels, int64_t n,
+                              int32_t num_classes, float* loss, float* dlogits,
+                              mck_stream_t stream);
+
+/* Human-readable name of a status code (static storage). */
+const char* mck_status_string(mck_status_t status);
+
+/* Detail of the calling thread's most recent failure (static per thread). */
+const char* mck_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCK_H */

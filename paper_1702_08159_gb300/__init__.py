@@ -1,0 +1,244 @@
+"""GB300-native McKernel / Fastfood feature maps (arXiv 1702.08159).
+
+Python binding of libmck.so: argument marshalling only. Every computation
+runs in the library's CUDA kernels; PyTorch provides device memory, streams
+and autograd. Calls run on the current CUDA stream of the tensors' device.
+
+    import paper_1702_08159_gb300 as mck
+    plan = mck.Plan(d=1024, E=16, kernel="rbf", sigma=1.0, seed=42)
+    phi = mck.features(plan, x)            # x: (n, in_dim) float32 CUDA
+    logits = mck.fused_logits(plan, x, W, b)
+
+The map is Z-hat = (1/(sigma sqrt d)) C H G Pi H B (Eq. etn:mckernel) and the
+features are [cos(Z-hat x-hat), sin(Z-hat x-hat)] per expansion
+(Eq. etn:mcfeatures); the classifier is softmax(W phi + b) (Sec. "Empirical
+Analysis and Experiments").
+"""
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import MckError, check, load
+
+__all__ = [
+    "Plan", "MckError", "fwht_", "features", "features_backward", "fused_logits",
+    "fused_logits_backward", "softmax_xent", "library_path",
+]
+
+_KERNELS = {"rbf": _lib.MCK_RBF, "matern": _lib.MCK_MATERN}
+
+
+def library_path():
+    return _lib.LIB_PATH
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _f32_cuda(t, name, device=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != torch.float32 or not t.is_cuda:
+        raise TypeError(f"{name} must be a float32 CUDA tensor")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{name} is on {t.device}, expected cuda:{device}")
+    return t
+
+
+def _rows(x, name="x"):
+    """(n, in_dim) view with unit stride in the last dimension; returns (n, in_dim, ldx)."""
+    if x.dim() != 2:
+        raise ValueError(f"{name} must be 2-D (n, in_dim)")
+    if x.stride(1) != 1 or (x.size(0) > 1 and x.stride(0) < x.size(1)):
+        x = x.contiguous()
+    ld = x.stride(0) if x.size(0) > 1 else x.size(1)
+    return x, x.size(0), x.size(1), ld
+
+
+class Plan:
+    """Tables B, Pi, G and C of E expansions of dimension d, made from a seed.
+
+    Sec. "API Description": a factory instantiates the parameters of a
+    pre-specified kernel; they are deterministic functions of a hash, so only
+    (d, E, kernel, sigma, t, seed) identify a plan.
+    """
+
+    def __init__(self, d, E, kernel="rbf", sigma=1.0, seed=0, matern_t=40, device=None):
+        lib = load()
+        if isinstance(kernel, str):
+            kernel = _KERNELS[kernel.lower()]
+        if device is None:
+            device = torch.cuda.current_device()
+        handle = ctypes.c_void_p()
+        check(lib.mck_plan_ex(ctypes.byref(handle), int(d), int(E), int(kernel), float(sigma),
+                              int(matern_t), int(seed) & 0xFFFFFFFFFFFFFFFF, int(device)),
+              "mck_plan")
+        self._h = handle
+        self.d, self.E, self.kernel, self.sigma = int(d), int(E), int(kernel), float(sigma)
+        self.matern_t = int(matern_t) if kernel == _lib.MCK_MATERN else 0
+        self.seed, self.device = int(seed), int(device)
+        self.L = self.d.bit_length() - 1
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("plan is closed")
+        return self._h
+
+    @property
+    def num_features(self):
+        return 2 * self.E * self.d
+
+    def tables(self):
+        """Host copies: B_bits (E, ceil(d/32)) uint32, perm (E, d) uint32, G and Cs (E, d) float32."""
+        words = (self.d + 31) // 32
+        B = np.empty((self.E, words), np.uint32)
+        P = np.empty((self.E, self.d), np.uint32)
+        G = np.empty((self.E, self.d), np.float32)
+        C = np.empty((self.E, self.d), np.float32)
+        check(load().mck_plan_tables(self.handle, B.ctypes.data, P.ctypes.data, G.ctypes.data,
+                                     C.ctypes.data), "mck_plan_tables")
+        return {"B_bits": B, "perm": P, "G": G, "Cs": C}
+
+    def signs(self):
+        """B as an (E, d) float32 array of +-1."""
+        bits = self.tables()["B_bits"]
+        k = np.arange(self.d)
+        return np.where((bits[:, k // 32] >> (k % 32)) & 1, -1.0, 1.0).astype(np.float32)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().mck_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __repr__(self):
+        k = "rbf" if self.kernel == _lib.MCK_RBF else f"matern(t={self.matern_t})"
+        return f"Plan(d={self.d}, E={self.E}, kernel={k}, sigma={self.sigma}, seed={self.seed})"
+
+
+def _tables(plan, Cs, G):
+    shape = (plan.E, plan.d)
+    for t, name in ((Cs, "Cs"), (G, "G")):
+        if t is not None:
+            _f32_cuda(t, name, plan.device)
+            if tuple(t.shape) != shape or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous ({plan.E}, {plan.d}) tensor")
+    return Cs, G
+
+
+def fwht_(x):
+    """In-place unnormalised Walsh-Hadamard transform of the rows of x (last dim d)."""
+    _f32_cuda(x, "x")
+    if not x.is_contiguous():
+        raise ValueError("x must be contiguous")
+    d = x.size(-1)
+    n = x.numel() // d if d else 0
+    check(load().mck_fwht(_ptr(x), n, d, _lib.MCK_FP32, _stream(x.device)), "mck_fwht")
+    return x
+
+
+def features(plan, x, Cs=None, G=None, out=None):
+    """phi(x): (n, 2 E d); row = E blocks of [cos | sin] (Eq. etn:mcfeatures)."""
+    _f32_cuda(x, "x", plan.device)
+    x, n, in_dim, ld = _rows(x)
+    Cs, G = _tables(plan, Cs, G)
+    if out is None:
+        out = torch.empty((n, plan.num_features), device=x.device, dtype=torch.float32)
+    else:
+        _f32_cuda(out, "out", plan.device)
+        if tuple(out.shape) != (n, plan.num_features) or not out.is_contiguous():
+            raise ValueError("out must be a contiguous (n, 2 E d) tensor")
+    check(load().mck_features(plan.handle, _ptr(x), n, in_dim, ld, _ptr(Cs), _ptr(G), _ptr(out),
+                              _stream(x.device)), "mck_features")
+    return out
+
+
+def features_backward(plan, x, dphi, Cs=None, G=None, need_dx=True, need_dCs=True, need_dG=True):
+    """(dx, dCs, dG) of sum(phi(x) * dphi); entries not requested are None."""
+    _f32_cuda(x, "x", plan.device)
+    x, n, in_dim, ld = _rows(x)
+    Cs, G = _tables(plan, Cs, G)
+    dphi = _f32_cuda(dphi, "dphi", plan.device).contiguous()
+    dev = x.device
+    dx = torch.empty((n, in_dim), device=dev, dtype=torch.float32) if need_dx else None
+    dCs = torch.empty((plan.E, plan.d), device=dev, dtype=torch.float32) if need_dCs else None
+    dG = torch.empty((plan.E, plan.d), device=dev, dtype=torch.float32) if need_dG else None
+    ldx = in_dim
+    if dx is not None and ld != in_dim:
+        x = x.contiguous()
+        ld = in_dim
+    check(load().mck_features_backward(plan.handle, _ptr(x), n, in_dim, ld, _ptr(Cs), _ptr(G),
+                                       _ptr(dphi), _ptr(dx), _ptr(dCs), _ptr(dG), _stream(dev)),
+          "mck_features_backward")
+    return dx, dCs, dG
+
+
+def fused_logits(plan, x, W, b=None, Cs=None, G=None, out=None):
+    """W phi(x) + b without materialising phi: (n, num_classes)."""
+    _f32_cuda(x, "x", plan.device)
+    x, n, in_dim, ld = _rows(x)
+    Cs, G = _tables(plan, Cs, G)
+    W = _f32_cuda(W, "W", plan.device).contiguous()
+    C = W.size(0)
+    if W.dim() != 2 or W.size(1) != plan.num_features:
+        raise ValueError(f"W must be (num_classes, {plan.num_features})")
+    if b is not None:
+        b = _f32_cuda(b, "b", plan.device).contiguous()
+    if out is None:
+        out = torch.empty((n, C), device=x.device, dtype=torch.float32)
+    check(load().mck_fused_logits(plan.handle, _ptr(x), n, in_dim, ld, _ptr(Cs), _ptr(G), _ptr(W),
+                                  _ptr(b), C, _ptr(out), _stream(x.device)), "mck_fused_logits")
+    return out
+
+
+def fused_logits_backward(plan, x, W, dlogits, Cs=None, G=None, need_dx=False, need_dCs=True,
+                          need_dG=True, need_dW=True, need_db=True):
+    """Gradients of sum(logits * dlogits) for fused_logits; dict of dx, dCs, dG, dW, db."""
+    _f32_cuda(x, "x", plan.device)
+    x, n, in_dim, ld = _rows(x)
+    Cs, G = _tables(plan, Cs, G)
+    W = _f32_cuda(W, "W", plan.device).contiguous()
+    dlogits = _f32_cuda(dlogits, "dlogits", plan.device).contiguous()
+    C = W.size(0)
+    dev = x.device
+    if need_dx and ld != in_dim:
+        x = x.contiguous()
+        ld = in_dim
+    mk = lambda need, shape: torch.empty(shape, device=dev, dtype=torch.float32) if need else None
+    g = {"dx": mk(need_dx, (n, in_dim)), "dCs": mk(need_dCs, (plan.E, plan.d)),
+         "dG": mk(need_dG, (plan.E, plan.d)), "dW": mk(need_dW, tuple(W.shape)),
+         "db": mk(need_db, (C,))}
+    check(load().mck_fused_logits_backward(
+        plan.handle, _ptr(x), n, in_dim, ld, _ptr(Cs), _ptr(G), _ptr(W), C, _ptr(dlogits),
+        _ptr(g["dx"]), _ptr(g["dCs"]), _ptr(g["dG"]), _ptr(g["dW"]), _ptr(g["db"]), _stream(dev)),
+        "mck_fused_logits_backward")
+    return g
+
+
+def softmax_xent(logits, labels, need_grad=True):
+    """(mean cross-entropy as a 0-d tensor, dlogits or None); labels int32."""
+    logits = _f32_cuda(logits, "logits").contiguous()
+    if labels.dtype != torch.int32 or labels.device != logits.device:
+        raise TypeError("labels must be int32 on the logits' device")
+    labels = labels.contiguous()
+    n, C = logits.shape
+    loss = torch.empty((), device=logits.device, dtype=torch.float32)
+    dl = torch.empty_like(logits) if need_grad else None
+    with torch.cuda.device(logits.device):
+        check(load().mck_softmax_xent(_ptr(logits), _ptr(labels), n, C, _ptr(loss), _ptr(dl),
+                                      _stream(logits.device)), "mck_softmax_xent")
+    return loss, dl

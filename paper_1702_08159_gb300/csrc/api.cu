@@ -1,0 +1,484 @@
+// extern "C" entry points of libmck.so (declared in include/mck.h).
+//
+// Every call validates its arguments on the host before queuing device work:
+// sizes, alignment, and that each array is device memory of the plan's
+// device whose allocation contains the whole extent the call will touch
+// (cuMemGetAddressRange). A wrong size or a host pointer therefore returns
+// MCK_EINVAL instead of reaching a kernel.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+namespace mck {
+namespace {
+
+thread_local std::string g_last_error;
+
+using AddressRangeFn = CUresult (*)(CUdeviceptr*, size_t*, CUdeviceptr);
+
+AddressRangeFn address_range_fn() {
+  static std::once_flag once;
+  static AddressRangeFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<AddressRangeFn>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+int sm_count(int device) {
+  static std::mutex mu;
+  static int cache[64] = {0};
+  std::lock_guard<std::mutex> lock(mu);
+  if (device < 0 || device >= 64) return 1;
+  if (!cache[device]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+      cudaGetLastError();
+      v = 1;
+    }
+    cache[device] = v;
+  }
+  return cache[device];
+}
+
+// Sets the plan's device current for the duration of a call and restores
+// the caller's device afterwards.
+struct DeviceScope {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      ok = false;
+      return;
+    }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) {
+      cudaGetLastError();
+      ok = false;
+    }
+  }
+  ~DeviceScope() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+int log2i(int64_t v) {
+  int l = 0;
+  while ((int64_t)1 << l < v) ++l;
+  return l;
+}
+
+// `p` must be device memory on `device` whose allocation holds [p, p + bytes).
+mck_status_t check_array(const void* p, int64_t bytes, int device, const char* name,
+                         bool allow_null = false) {
+  if (!p) {
+    if (allow_null) return MCK_OK;
+    return fail(MCK_EINVAL, std::string(name) + " is NULL");
+  }
+  if (bytes <= 0) return MCK_OK;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MCK_EINVAL, std::string(name) + " is not a CUDA pointer");
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    return fail(MCK_EINVAL, std::string(name) + " is not device memory");
+  if (at.type == cudaMemoryTypeDevice && at.device != device)
+    return fail(MCK_EINVAL, std::string(name) + " lives on device " + std::to_string(at.device) +
+                                ", the call runs on device " + std::to_string(device));
+  if (AddressRangeFn fn = address_range_fn()) {
+    CUdeviceptr base = 0;
+    size_t size = 0;
+    if (fn(&base, &size, (CUdeviceptr)p) == CUDA_SUCCESS) {
+      const uint64_t lo = (uint64_t)(uintptr_t)p, end = (uint64_t)base + size;
+      if (lo + (uint64_t)bytes > end)
+        return fail(MCK_EINVAL, std::string(name) + ": " + std::to_string(bytes) +
+                                    " bytes from this address run past the end of its allocation");
+    }
+  }
+  return MCK_OK;
+}
+
+#define MCK_TRY(expr)                    \
+  do {                                   \
+    const mck_status_t _s = (expr);      \
+    if (_s != MCK_OK) return _s;         \
+  } while (0)
+
+mck_status_t check_plan(const mck_plan_s* p) {
+  if (!p) return fail(MCK_EINVAL, "plan is NULL");
+  return MCK_OK;
+}
+
+mck_status_t check_x(const mck_plan_s* p, const float* x, int64_t n, int64_t in_dim, int64_t ldx) {
+  if (n < 0) return fail(MCK_EINVAL, "n < 0");
+  if (in_dim < 1 || in_dim > p->d) return fail(MCK_EINVAL, "in_dim must be in [1, d]");
+  if (ldx < in_dim) return fail(MCK_EINVAL, "ldx < in_dim");
+  if (n == 0) return x ? MCK_OK : fail(MCK_EINVAL, "x is NULL");
+  return check_array(x, 4 * ((n - 1) * ldx + in_dim), p->device, "x");
+}
+
+FeatureArgs feature_args(const mck_plan_s* p, const float* x, int64_t n, int64_t in_dim,
+                         int64_t ldx, const float* Cs, const float* G) {
+  FeatureArgs a{};
+  a.x = x;
+  a.n = n;
+  a.in_dim = in_dim;
+  a.ldx = ldx;
+  a.B_bits = p->B_bits;
+  a.perm = p->perm;
+  a.G = G ? G : p->G;
+  a.Cs = Cs ? Cs : p->Cs;
+  a.E = p->E;
+  a.L = p->L;
+  a.num_sms = p->num_sms;
+  return a;
+}
+
+mck_status_t check_tables(const mck_plan_s* p, const float* Cs, const float* G) {
+  const int64_t bytes = 4 * p->d * p->E;
+  MCK_TRY(check_array(Cs, bytes, p->device, "Cs", true));
+  MCK_TRY(check_array(G, bytes, p->device, "G", true));
+  if ((Cs && (uintptr_t)Cs % 16) || (G && (uintptr_t)G % 16))
+    return fail(MCK_EINVAL, "Cs and G must be 16-byte aligned");
+  return MCK_OK;
+}
+
+mck_status_t launched(cudaError_t err, const char* where) {
+  return err == cudaSuccess ? MCK_OK : cuda_fail(err, where);
+}
+
+// Stream-ordered scratch, freed on the same stream when the owner goes out of scope.
+struct Scratch {
+  void* ptr = nullptr;
+  cudaStream_t s;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  mck_status_t alloc(size_t bytes) {
+    if (bytes == 0) return MCK_OK;
+    if (cudaMallocAsync(&ptr, bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      ptr = nullptr;
+      return fail(MCK_ENOMEM, "scratch allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    return MCK_OK;
+  }
+  ~Scratch() {
+    if (ptr) cudaFreeAsync(ptr, s);
+  }
+};
+
+}  // namespace
+
+mck_status_t fail(mck_status_t s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+mck_status_t cuda_fail(cudaError_t err, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorName(err) + " (" + cudaGetErrorString(err) + ")";
+  return MCK_ECUDA;
+}
+
+}  // namespace mck
+
+using namespace mck;
+
+extern "C" {
+
+const char* mck_status_string(mck_status_t s) {
+  switch (s) {
+    case MCK_OK: return "MCK_OK";
+    case MCK_EINVAL: return "MCK_EINVAL: invalid argument";
+    case MCK_ENOMEM: return "MCK_ENOMEM: out of memory";
+    case MCK_ECUDA: return "MCK_ECUDA: CUDA runtime error";
+    case MCK_ETIMEOUT: return "MCK_ETIMEOUT: bounded wait expired";
+    case MCK_EUNSUPPORTED: return "MCK_EUNSUPPORTED: not supported by this version";
+  }
+  return "unknown mck_status_t";
+}
+
+const char* mck_last_error(void) { return g_last_error.c_str(); }
+
+mck_status_t mck_plan_ex(mck_plan_t* out, int64_t d, int32_t E, int32_t kernel, double sigma,
+                         int32_t matern_t, uint64_t seed, int32_t device) {
+  if (!out) return fail(MCK_EINVAL, "out is NULL");
+  if (!is_pow2(d) || d < 2) return fail(MCK_EINVAL, "d must be a power of two >= 2");
+  if (d > ((int64_t)1 << MCK_MAX_LOG2_D))
+    return fail(MCK_EUNSUPPORTED, "plans support d <= 2^15");
+  if (E < 1 || E > 65536) return fail(MCK_EINVAL, "E must be in [1, 65536]");
+  if ((int64_t)E * d > ((int64_t)1 << 28)) return fail(MCK_EINVAL, "E * d must be <= 2^28");
+  if (kernel != MCK_RBF && kernel != MCK_MATERN) return fail(MCK_EINVAL, "unknown kernel");
+  if (!(sigma > 0.0) || !std::isfinite(sigma)) return fail(MCK_EINVAL, "sigma must be finite and > 0");
+  if (kernel == MCK_MATERN && (matern_t < 1 || matern_t > 4096))
+    return fail(MCK_EINVAL, "Matern t must be in [1, 4096]");
+  if (device < -1) return fail(MCK_EINVAL, "device must be >= -1");
+  int ndev = 0;
+  cudaError_t err = cudaGetDeviceCount(&ndev);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(err, "cudaGetDeviceCount");
+  }
+  if (device >= ndev) return fail(MCK_EINVAL, "no such device");
+  if (device < 0 && (err = cudaGetDevice(&device)) != cudaSuccess) return cuda_fail(err, "cudaGetDevice");
+  DeviceScope scope(device);
+  if (!scope.ok) return fail(MCK_ECUDA, "cannot select the device");
+
+  mck_plan_s* p = new (std::nothrow) mck_plan_s();
+  if (!p) return fail(MCK_ENOMEM, "plan allocation failed");
+  p->d = d;
+  p->L = log2i(d);
+  p->E = E;
+  p->kernel = kernel;
+  p->sigma = sigma;
+  p->matern_t = kernel == MCK_MATERN ? matern_t : 0;
+  p->seed = seed;
+  p->device = device;
+  p->num_sms = sm_count(device);
+  p->words = (d + 31) / 32;
+  const size_t n = (size_t)d * E;
+  bool ok = cudaMalloc(&p->B_bits, sizeof(uint32_t) * p->words * E) == cudaSuccess &&
+            cudaMalloc(&p->perm, sizeof(uint32_t) * n) == cudaSuccess &&
+            cudaMalloc(&p->G, sizeof(float) * n) == cudaSuccess &&
+            cudaMalloc(&p->Cs, sizeof(float) * n) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    mck_plan_destroy(p);
+    return fail(MCK_ENOMEM, "plan table allocation failed");
+  }
+  cudaStream_t s = nullptr;
+  if ((err = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) {
+    mck_plan_destroy(p);
+    return cuda_fail(err, "cudaStreamCreate");
+  }
+  const mck_status_t st = build_tables(p, s);
+  cudaStreamDestroy(s);
+  if (st != MCK_OK) {
+    mck_plan_destroy(p);
+    return st;
+  }
+  *out = p;
+  return MCK_OK;
+}
+
+mck_status_t mck_plan(mck_plan_t* out, int64_t d, int32_t E, int32_t kernel, double sigma,
+                      uint64_t seed) {
+  return mck_plan_ex(out, d, E, kernel, sigma, 40, seed, -1);
+}
+
+void mck_plan_destroy(mck_plan_t p) {
+  if (!p) return;
+  {
+    DeviceScope scope(p->device);
+    cudaDeviceSynchronize();
+    cudaFree(p->B_bits);
+    cudaFree(p->perm);
+    cudaFree(p->G);
+    cudaFree(p->Cs);
+    cudaGetLastError();
+  }
+  delete p;
+}
+
+mck_status_t mck_plan_info(mck_plan_t p, int64_t* d, int32_t* E, int32_t* kernel, double* sigma,
+                           int32_t* matern_t, uint64_t* seed, int32_t* device) {
+  MCK_TRY(check_plan(p));
+  if (d) *d = p->d;
+  if (E) *E = p->E;
+  if (kernel) *kernel = p->kernel;
+  if (sigma) *sigma = p->sigma;
+  if (matern_t) *matern_t = p->matern_t;
+  if (seed) *seed = p->seed;
+  if (device) *device = p->device;
+  return MCK_OK;
+}
+
+mck_status_t mck_plan_tables(mck_plan_t p, uint32_t* B_bits, uint32_t* perm, float* G, float* Cs) {
+  MCK_TRY(check_plan(p));
+  DeviceScope scope(p->device);
+  const size_t n = (size_t)p->d * p->E;
+  cudaError_t err = cudaSuccess;
+  if (B_bits && err == cudaSuccess)
+    err = cudaMemcpy(B_bits, p->B_bits, sizeof(uint32_t) * p->words * p->E, cudaMemcpyDeviceToHost);
+  if (perm && err == cudaSuccess)
+    err = cudaMemcpy(perm, p->perm, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost);
+  if (G && err == cudaSuccess) err = cudaMemcpy(G, p->G, sizeof(float) * n, cudaMemcpyDeviceToHost);
+  if (Cs && err == cudaSuccess) err = cudaMemcpy(Cs, p->Cs, sizeof(float) * n, cudaMemcpyDeviceToHost);
+  return launched(err, "mck_plan_tables");
+}
+
+mck_status_t mck_fwht(float* x, int64_t n, int64_t d, int32_t prec, mck_stream_t stream) {
+  if (prec != MCK_FP32) return fail(MCK_EUNSUPPORTED, "only MCK_FP32 is implemented");
+  if (!is_pow2(d)) return fail(MCK_EINVAL, "d must be a power of two");
+  if (d > ((int64_t)1 << MCK_MAX_LOG2_D_FWHT)) return fail(MCK_EUNSUPPORTED, "d must be <= 2^20");
+  if (n < 0) return fail(MCK_EINVAL, "n < 0");
+  if (!x) return fail(MCK_EINVAL, "x is NULL");
+  if (n == 0 || d == 1) return MCK_OK;
+  if (d >= 4 && (uintptr_t)x % 16) return fail(MCK_EINVAL, "x must be 16-byte aligned");
+  int device = 0;
+  cudaError_t err = cudaGetDevice(&device);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaGetDevice");
+  MCK_TRY(check_array(x, 4 * n * d, device, "x"));
+  return launched(launch_fwht(x, n, log2i(d), sm_count(device), (cudaStream_t)stream), "mck_fwht");
+}
+
+mck_status_t mck_features(mck_plan_t p, const float* x, int64_t n, int64_t in_dim, int64_t ldx,
+                          const float* Cs, const float* G, float* phi, mck_stream_t stream) {
+  MCK_TRY(check_plan(p));
+  DeviceScope scope(p->device);
+  MCK_TRY(check_x(p, x, n, in_dim, ldx));
+  MCK_TRY(check_tables(p, Cs, G));
+  const int64_t F = 2 * p->E * p->d;
+  if (n == 0) return MCK_OK;
+  MCK_TRY(check_array(phi, 4 * n * F, p->device, "phi"));
+  if (p->d >= 4 && (uintptr_t)phi % 16) return fail(MCK_EINVAL, "phi must be 16-byte aligned");
+  return launched(launch_features(feature_args(p, x, n, in_dim, ldx, Cs, G), phi,
+                                  (cudaStream_t)stream),
+                  "mck_features");
+}
+
+static int64_t num_partials(const mck_plan_s* p, int64_t n) {
+  const int T = 1 << (p->L - 5);
+  const int vpw = 32 / T;
+  const int spi = vpw >= 8 ? vpw : 8;
+  const int64_t tiles = (n + spi - 1) / spi;
+  const int64_t target = (int64_t)p->num_sms * 8;
+  int64_t wpe = (target + p->E - 1) / p->E;
+  wpe = wpe < 1 ? 1 : (wpe > tiles ? tiles : wpe);
+  return wpe * p->E;
+}
+
+static mck_status_t run_backward(mck_plan_s* p, BackwardArgs b, cudaStream_t s, const char* who) {
+  const int64_t n = b.f.n;
+  if (n == 0) return MCK_OK;
+  const bool params = b.dCs || b.dG || b.phi_out;
+  const int64_t np = params ? num_partials(p, n) : 0;
+  Scratch part(s);
+  MCK_TRY(part.alloc(sizeof(float) * (size_t)np * 2 * p->d));
+  return launched(launch_backward(b, (float*)part.ptr, np, s), who);
+}
+
+mck_status_t mck_features_backward(mck_plan_t p, const float* x, int64_t n, int64_t in_dim,
+                                   int64_t ldx, const float* Cs, const float* G, const float* dphi,
+                                   float* dx, float* dCs, float* dG, mck_stream_t stream) {
+  MCK_TRY(check_plan(p));
+  if (p->L < 5 || p->L > 10) return fail(MCK_EUNSUPPORTED, "the adjoint supports 32 <= d <= 1024");
+  DeviceScope scope(p->device);
+  MCK_TRY(check_x(p, x, n, in_dim, ldx));
+  MCK_TRY(check_tables(p, Cs, G));
+  const int64_t F = 2 * p->E * p->d, tb = 4 * p->E * p->d;
+  MCK_TRY(check_array(dCs, tb, p->device, "dCs", true));
+  MCK_TRY(check_array(dG, tb, p->device, "dG", true));
+  if (n == 0) return MCK_OK;
+  MCK_TRY(check_array(dphi, 4 * n * F, p->device, "dphi"));
+  if ((uintptr_t)dphi % 16) return fail(MCK_EINVAL, "dphi must be 16-byte aligned");
+  MCK_TRY(check_array(dx, 4 * ((n - 1) * ldx + in_dim), p->device, "dx", true));
+  BackwardArgs b{};
+  b.f = feature_args(p, x, n, in_dim, ldx, Cs, G);
+  b.dphi = dphi;
+  b.dx = dx;
+  b.dCs = dCs;
+  b.dG = dG;
+  return run_backward(p, b, (cudaStream_t)stream, "mck_features_backward");
+}
+
+mck_status_t mck_fused_logits(mck_plan_t p, const float* x, int64_t n, int64_t in_dim, int64_t ldx,
+                              const float* Cs, const float* G, const float* W, const float* b,
+                              int32_t C, float* logits, mck_stream_t stream) {
+  MCK_TRY(check_plan(p));
+  if (C < 1 || C > MCK_MAX_CLASSES) return fail(MCK_EINVAL, "num_classes must be in [1, 16]");
+  DeviceScope scope(p->device);
+  MCK_TRY(check_x(p, x, n, in_dim, ldx));
+  MCK_TRY(check_tables(p, Cs, G));
+  const int64_t F = 2 * p->E * p->d;
+  MCK_TRY(check_array(W, 4 * C * F, p->device, "W"));
+  if (p->d >= 4 && (uintptr_t)W % 16) return fail(MCK_EINVAL, "W must be 16-byte aligned");
+  MCK_TRY(check_array(b, 4 * C, p->device, "b", true));
+  if (n == 0) return MCK_OK;
+  MCK_TRY(check_array(logits, 4 * n * C, p->device, "logits"));
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch part(s);
+  MCK_TRY(part.alloc(sizeof(float) * (size_t)n * p->E * C));
+  return launched(launch_logits(feature_args(p, x, n, in_dim, ldx, Cs, G), W, b, C,
+                                (float*)part.ptr, logits, s),
+                  "mck_fused_logits");
+}
+
+mck_status_t mck_fused_logits_backward(mck_plan_t p, const float* x, int64_t n, int64_t in_dim,
+                                       int64_t ldx, const float* Cs, const float* G, const float* W,
+                                       int32_t C, const float* dlogits, float* dx, float* dCs,
+                                       float* dG, float* dW, float* db, mck_stream_t stream) {
+  MCK_TRY(check_plan(p));
+  if (p->L < 5 || p->L > 10) return fail(MCK_EUNSUPPORTED, "the adjoint supports 32 <= d <= 1024");
+  if (C < 1 || C > MCK_MAX_CLASSES) return fail(MCK_EINVAL, "num_classes must be in [1, 16]");
+  DeviceScope scope(p->device);
+  MCK_TRY(check_x(p, x, n, in_dim, ldx));
+  MCK_TRY(check_tables(p, Cs, G));
+  const int64_t F = 2 * p->E * p->d, tb = 4 * p->E * p->d;
+  MCK_TRY(check_array(W, 4 * C * F, p->device, "W"));
+  if ((uintptr_t)W % 16) return fail(MCK_EINVAL, "W must be 16-byte aligned");
+  MCK_TRY(check_array(dCs, tb, p->device, "dCs", true));
+  MCK_TRY(check_array(dG, tb, p->device, "dG", true));
+  MCK_TRY(check_array(dW, 4 * C * F, p->device, "dW", true));
+  MCK_TRY(check_array(db, 4 * C, p->device, "db", true));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0) {
+    // Gradients of an empty batch are zero.
+    cudaError_t err = cudaSuccess;
+    if (dCs) err = cudaMemsetAsync(dCs, 0, tb, s);
+    if (dG && err == cudaSuccess) err = cudaMemsetAsync(dG, 0, tb, s);
+    if (dW && err == cudaSuccess) err = cudaMemsetAsync(dW, 0, 4 * C * F, s);
+    if (db && err == cudaSuccess) err = cudaMemsetAsync(db, 0, 4 * C, s);
+    return launched(err, "mck_fused_logits_backward");
+  }
+  MCK_TRY(check_array(dlogits, 4 * n * C, p->device, "dlogits"));
+  MCK_TRY(check_array(dx, 4 * ((n - 1) * ldx + in_dim), p->device, "dx", true));
+  Scratch phi(s);
+  if (dW) MCK_TRY(phi.alloc(sizeof(float) * (size_t)n * F));
+  BackwardArgs b{};
+  b.f = feature_args(p, x, n, in_dim, ldx, Cs, G);
+  b.W = W;
+  b.dlogits = dlogits;
+  b.C = C;
+  b.phi_out = (float*)phi.ptr;
+  b.dx = dx;
+  b.dCs = dCs;
+  b.dG = dG;
+  MCK_TRY(run_backward(p, b, s, "mck_fused_logits_backward"));
+  return launched(launch_logit_weight_grads(dlogits, (const float*)phi.ptr, n, C, F, dW, db, s),
+                  "mck_fused_logits_backward");
+}
+
+mck_status_t mck_softmax_xent(const float* logits, const int32_t* labels, int64_t n, int32_t C,
+                              float* loss, float* dlogits, mck_stream_t stream) {
+  if (n < 0) return fail(MCK_EINVAL, "n < 0");
+  if (C < 1) return fail(MCK_EINVAL, "num_classes must be >= 1");
+  int device = 0;
+  cudaError_t err = cudaGetDevice(&device);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaGetDevice");
+  MCK_TRY(check_array(loss, 4, device, "loss", true));
+  if (n == 0) {
+    if (loss) return launched(cudaMemsetAsync(loss, 0, 4, (cudaStream_t)stream), "mck_softmax_xent");
+    return MCK_OK;
+  }
+  MCK_TRY(check_array(logits, 4 * n * C, device, "logits"));
+  MCK_TRY(check_array(labels, 4 * n, device, "labels"));
+  MCK_TRY(check_array(dlogits, 4 * n * C, device, "dlogits", true));
+  return launched(launch_softmax_xent(logits, labels, n, C, loss, dlogits, (cudaStream_t)stream),
+                  "mck_softmax_xent");
+}
+
+}  // extern "C"

@@ -1,0 +1,217 @@
+// Device building blocks shared by the transform, feature and adjoint kernels.
+//
+// A vector of d = 2^L floats (5 <= L <= 15) is held by T = 2^(L-5) threads,
+// 32 registers each. Bit b of an element index k is either a "register bit"
+// (selected by the register index j) or a "thread bit" (selected by the
+// thread index lam within the vector's thread group). The Hadamard transform
+// factorises over index bits (H_d = H_2 (x) ... (x) H_2, Sec. "Fast Walsh
+// Hadamard": each level of the recursion pairs indices that differ in one
+// bit), so H is applied by transforming the register bits of one layout in
+// registers, moving the data through shared memory into a layout where other
+// bits are register bits, and repeating until every bit was transformed once.
+//
+// Layout A  register bits {0,1} u [L-3, L); thread bits [2, L-3).
+//           Four consecutive elements per register quad: 128-bit global
+//           loads/stores, coalesced across the thread group.
+// Layout B  register bits [s, s+5), s = min(2, L-5); thread bits the rest.
+// Layout C  register bits [L-8, L-3) (only L >= 11).
+// L <= 10: phase A transforms A's register bits outside B's, phase B all of B's.
+// L >= 11: A transforms {0,1,L-3..L-1}, B [2,7), C [7, L-3).
+//
+// Shared memory: element k of vector slot g sits at word
+//   g * SLOT + k + 4 * (k >> 7),      SLOT = d + max(4, d/32),
+// i.e. four padding words after every 128. Because the thread bits and the
+// register bits of an index are disjoint, each access is a per-thread base
+// plus a compile-time offset, and the layout-A (128-bit) and layout-B/C
+// (32-bit) accesses of a warp are free of bank conflicts for L >= 8 (2-way
+// for L = 6, 7; L = 5 needs no layout moves).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace mck {
+
+constexpr float kTwoPiHi = 6.28125f;                    // 201/32, exact
+constexpr float kTwoPiLo = 1.9353071795864769253e-3f;   // 2 pi - kTwoPiHi
+constexpr float kInvTwoPi = 0.15915494309189533577f;
+
+template <int L>
+struct Lay {
+  static_assert(L >= 5 && L <= 15, "register layouts cover 5 <= L <= 15");
+  static constexpr int d = 1 << L;
+  static constexpr int T = 1 << (L - 5);            // threads per vector
+  static constexpr int S = (L - 5 < 2) ? (L - 5) : 2;
+  static constexpr int CQ = (L >= 11) ? (L - 8) : 0;  // layout C first register bit
+  static constexpr int SLOT = d + ((d / 32) > 4 ? (d / 32) : 4);  // padded words per vector
+
+  // Element index of register j of thread lam, split into the disjoint
+  // thread-selected and register-selected bits (k = k_t(lam) + k_r(j)).
+  __host__ __device__ static constexpr int kA_t(int lam) { return lam << 2; }
+  __host__ __device__ static constexpr int kA_r(int j) { return (j & 3) | ((j >> 2) << (L - 3)); }
+  __host__ __device__ static constexpr int kB_t(int lam) {
+    return (lam & ((1 << S) - 1)) | ((lam >> S) << (S + 5));
+  }
+  __host__ __device__ static constexpr int kB_r(int j) { return j << S; }
+  __host__ __device__ static constexpr int kC_t(int lam) {
+    return (lam & ((1 << CQ) - 1)) | ((lam >> CQ) << (CQ + 5));
+  }
+  __host__ __device__ static constexpr int kC_r(int j) { return j << CQ; }
+  __host__ __device__ static constexpr int kA(int lam, int j) { return kA_t(lam) + kA_r(j); }
+  __host__ __device__ static constexpr int kB(int lam, int j) { return kB_t(lam) + kB_r(j); }
+  __host__ __device__ static constexpr int kC(int lam, int j) { return kC_t(lam) + kC_r(j); }
+  // Index bit that register bit jb of layout A selects.
+  static constexpr int a_bit(int jb) { return jb < 2 ? jb : (L - 3 + jb - 2); }
+  static constexpr unsigned maskA() {
+    unsigned m = 0;
+    for (int jb = 0; jb < 5; ++jb) {
+      const int kb = a_bit(jb);
+      const bool in_b = (L <= 10) && kb >= S && kb < S + 5;
+      if (!in_b) m |= 1u << jb;
+    }
+    return m;
+  }
+  static constexpr unsigned maskB() { return 31u; }
+  static constexpr unsigned maskC() {
+    unsigned m = 0;
+    if (L >= 11)
+      for (int jb = 0; jb < 5; ++jb)
+        if (CQ + jb >= 7) m |= 1u << jb;
+    return m;
+  }
+};
+
+// Padded word offset of element k inside its vector slot (see header). For
+// k = a + b with disjoint bits, pad(k) = pad(a) + pad(b).
+__host__ __device__ __forceinline__ constexpr int pad(int k) { return k + 4 * (k >> 7); }
+
+// Word offset of element k of vector slot g.
+template <int L>
+__host__ __device__ __forceinline__ constexpr int spos(int g, int k) {
+  return g * Lay<L>::SLOT + pad(k);
+}
+
+// H over the register bits in MASK (unnormalised butterflies).
+template <unsigned MASK>
+__device__ __forceinline__ void hreg(float (&w)[32]) {
+#pragma unroll
+  for (int b = 0; b < 5; ++b) {
+    if (MASK >> b & 1u) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        if (!(j >> b & 1)) {
+          const float a = w[j], c = w[j | (1 << b)];
+          w[j] = a + c;
+          w[j | (1 << b)] = a - c;
+        }
+      }
+    }
+  }
+}
+
+template <unsigned MASK>
+__host__ __device__ constexpr int lowest_bit() {
+  return (MASK & 1u) ? 0 : (MASK & 2u) ? 1 : (MASK & 4u) ? 2 : (MASK & 8u) ? 3 : 4;
+}
+
+// H over MASK applied to (s * w): the scale is folded into the first
+// butterfly stage (a' = s_a w_a + s_c w_c, c' = s_a w_a - s_c w_c).
+template <unsigned MASK>
+__device__ __forceinline__ void hreg_scaled(float (&w)[32], const float (&s)[32]) {
+  static_assert(MASK != 0, "scaled transform needs at least one bit");
+  constexpr int b0 = lowest_bit<MASK>();
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    if (!(j >> b0 & 1)) {
+      const int jc = j | (1 << b0);
+      const float a = s[j] * w[j];
+      const float c = w[jc];
+      w[j] = fmaf(s[jc], c, a);
+      w[jc] = fmaf(-s[jc], c, a);
+    }
+  }
+  hreg<MASK & ~(1u << b0)>(w);
+}
+
+// cos and sin of z: z is reduced to r = z - 2 pi k in [-pi, pi] (Cody & Waite
+// two-constant reduction, both products exact for |k| < 2^15), then the
+// hardware approximations, whose absolute error is below 2^-21 on [-pi, pi].
+__device__ __forceinline__ void cos_sin(float z, float& c, float& s) {
+  const float k = rintf(z * kInvTwoPi);
+  float r = fmaf(-k, kTwoPiHi, z);
+  r = fmaf(-k, kTwoPiLo, r);
+  c = __cosf(r);
+  s = __sinf(r);
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void sts32(uint32_t addr, float v) {
+  asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ float lds32(uint32_t addr) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  return v;
+}
+// Streaming (evict-first) 128-bit global store: the feature matrix is written
+// once and not re-read by the kernel, so it should not displace the tables.
+__device__ __forceinline__ void stg128_cs(float* p, float a, float b, float c, float d) {
+  asm volatile("st.global.cs.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
+               "f"(d)
+               : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Layout moves through shared memory. `buf` points at the caller's shared
+// buffer; g is the vector slot of this thread's group. Callers separate a
+// store phase from the next load phase with the appropriate barrier.
+// ---------------------------------------------------------------------------
+template <int L>
+__device__ __forceinline__ void store_A(float* buf, int g, int lam, const float (&w)[32]) {
+  float* p = buf + g * Lay<L>::SLOT + pad(Lay<L>::kA_t(lam));
+#pragma unroll
+  for (int m = 0; m < 8; ++m)
+    *reinterpret_cast<float4*>(p + pad(Lay<L>::kA_r(4 * m))) =
+        make_float4(w[4 * m], w[4 * m + 1], w[4 * m + 2], w[4 * m + 3]);
+}
+template <int L>
+__device__ __forceinline__ void load_A(const float* buf, int g, int lam, float (&w)[32]) {
+  const float* p = buf + g * Lay<L>::SLOT + pad(Lay<L>::kA_t(lam));
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const float4 v = *reinterpret_cast<const float4*>(p + pad(Lay<L>::kA_r(4 * m)));
+    w[4 * m] = v.x;
+    w[4 * m + 1] = v.y;
+    w[4 * m + 2] = v.z;
+    w[4 * m + 3] = v.w;
+  }
+}
+template <int L>
+__device__ __forceinline__ void store_B(float* buf, int g, int lam, const float (&w)[32]) {
+  float* p = buf + g * Lay<L>::SLOT + pad(Lay<L>::kB_t(lam));
+#pragma unroll
+  for (int j = 0; j < 32; ++j) p[pad(Lay<L>::kB_r(j))] = w[j];
+}
+template <int L>
+__device__ __forceinline__ void load_B(const float* buf, int g, int lam, float (&w)[32]) {
+  const float* p = buf + g * Lay<L>::SLOT + pad(Lay<L>::kB_t(lam));
+#pragma unroll
+  for (int j = 0; j < 32; ++j) w[j] = p[pad(Lay<L>::kB_r(j))];
+}
+template <int L>
+__device__ __forceinline__ void store_C(float* buf, int lam, const float (&w)[32]) {
+  float* p = buf + pad(Lay<L>::kC_t(lam));
+#pragma unroll
+  for (int j = 0; j < 32; ++j) p[pad(Lay<L>::kC_r(j))] = w[j];
+}
+template <int L>
+__device__ __forceinline__ void load_C(const float* buf, int lam, float (&w)[32]) {
+  const float* p = buf + pad(Lay<L>::kC_t(lam));
+#pragma unroll
+  for (int j = 0; j < 32; ++j) w[j] = p[pad(Lay<L>::kC_r(j))];
+}
+
+}  // namespace mck

@@ -1,0 +1,505 @@
+// Fused Fastfood feature kernels: for each sample n and expansion e,
+//
+//   u  = H (B_e x-hat)        x-hat = x padded with zeros to d   (Eq. etn:mckernel)
+//   v  = Pi_e u               v_k = u_{pi_e(k)}
+//   h  = H (G_e v)
+//   z  = Cs_e h               Cs = C/(sigma sqrt d)
+//   phi[n, e] = [cos z | sin z]                                  (Eq. etn:mcfeatures)
+//
+// in one pass: x is read, the two transforms, the permutation and the
+// diagonals run in registers and shared memory, and only phi is written
+// (MODE_FEATURES) -- or phi is contracted with the classifier weights on the
+// fly and only per-(sample, expansion) partial logits are written
+// (MODE_LOGITS; Sec. "Empirical Analysis": softmax(W phi + b)).
+//
+// Kernels by L = log2 d:
+//   L = 5..10  warp kernel. 2^(L-5) lanes hold one vector (32 registers
+//              each); a warp processes 32/2^(L-5) samples at once. Work items
+//              are (tile of samples, expansion); a warp loads the expansion's
+//              tables into registers once per item (B as a bit mask, G, Cs and
+//              the gather addresses of Pi) and runs the item's samples.
+//   L = 11..15 block kernel: one block of 2^(L-5) threads per (sample, e).
+//   L = 1..4   one thread per (sample, e).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace mck {
+namespace {
+
+constexpr int MODE_FEATURES = 0;
+constexpr int MODE_LOGITS = 1;
+constexpr int kWarps = 4;   // warps per block of the warp kernel
+constexpr int CMAX = MCK_MAX_CLASSES;
+
+struct Launch {
+  FeatureArgs a;
+  bool vec_x;         // x rows 16-byte aligned and in_dim % 4 == 0
+  float* phi;         // MODE_FEATURES: n x 2Ed
+  const float* W;     // MODE_LOGITS: C x 2Ed
+  float* part;        // MODE_LOGITS: n x E x C
+  int C;
+};
+
+// Flip the sign of register j where bit j of `mask` is set (B = -1).
+__device__ __forceinline__ void apply_signs(float (&w)[32], uint32_t mask) {
+#pragma unroll
+  for (int j = 0; j < 32; ++j)
+    w[j] = __int_as_float(__float_as_int(w[j]) ^ ((mask << (31 - j)) & 0x80000000u));
+}
+
+// B bits of the elements of layout A held by thread lam, as a 32-bit mask.
+template <int L>
+__device__ __forceinline__ uint32_t load_bmask_A(const uint32_t* __restrict__ Bw, int lam) {
+  uint32_t mask = 0;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int k0 = Lay<L>::kA(lam, 4 * m);  // multiple of 4: the 4 bits share a word
+    mask |= ((__ldg(Bw + (k0 >> 5)) >> (k0 & 31)) & 0xFu) << (4 * m);
+  }
+  return mask;
+}
+
+// x-hat in layout A (zero past in_dim, zero for an invalid sample).
+template <int L>
+__device__ __forceinline__ void load_x_A(const Launch& P, int64_t n, bool valid, int lam,
+                                         float (&w)[32]) {
+  const float* row = P.a.x + n * P.a.ldx;
+  const int64_t in_dim = P.a.in_dim;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int k0 = Lay<L>::kA(lam, 4 * m);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+      if (P.vec_x) {
+        if (k0 < in_dim) v = __ldg(reinterpret_cast<const float4*>(row + k0));
+      } else {
+        if (k0 + 0 < in_dim) v.x = __ldg(row + k0 + 0);
+        if (k0 + 1 < in_dim) v.y = __ldg(row + k0 + 1);
+        if (k0 + 2 < in_dim) v.z = __ldg(row + k0 + 2);
+        if (k0 + 3 < in_dim) v.w = __ldg(row + k0 + 3);
+      }
+    }
+    w[4 * m] = v.x;
+    w[4 * m + 1] = v.y;
+    w[4 * m + 2] = v.z;
+    w[4 * m + 3] = v.w;
+  }
+}
+
+// Epilogue on layout A: z = Cs h, then either store [cos | sin] or fold them
+// into the per-class partial sums acc[c] += <W_c, phi>.
+template <int L, int MODE>
+__device__ __forceinline__ void epilogue_A(const Launch& P, int64_t n, int e, bool valid, int lam,
+                                           const float (&h)[32], const float (&cs)[32],
+                                           float (&acc)[CMAX]) {
+  constexpr int d = 1 << L;
+  const int64_t F = 2ll * P.a.E * d;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int k0 = Lay<L>::kA(lam, 4 * m);
+    float c[4], s[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cos_sin(cs[4 * m + q] * h[4 * m + q], c[q], s[q]);
+    if constexpr (MODE == MODE_FEATURES) {
+      if (valid) {
+        float* o = P.phi + n * F + 2ll * e * d + k0;
+        __stcs(reinterpret_cast<float4*>(o), make_float4(c[0], c[1], c[2], c[3]));
+        __stcs(reinterpret_cast<float4*>(o + d), make_float4(s[0], s[1], s[2], s[3]));
+      }
+    } else {
+      const float* wr = P.W + 2ll * e * d + k0;
+#pragma unroll
+      for (int cl = 0; cl < CMAX; ++cl) {
+        if (cl < P.C) {
+          const float4 wc = __ldg(reinterpret_cast<const float4*>(wr + cl * F));
+          const float4 ws = __ldg(reinterpret_cast<const float4*>(wr + cl * F + d));
+          float t = acc[cl];
+          t = fmaf(wc.x, c[0], t);
+          t = fmaf(wc.y, c[1], t);
+          t = fmaf(wc.z, c[2], t);
+          t = fmaf(wc.w, c[3], t);
+          t = fmaf(ws.x, s[0], t);
+          t = fmaf(ws.y, s[1], t);
+          t = fmaf(ws.z, s[2], t);
+          t = fmaf(ws.w, s[3], t);
+          acc[cl] = t;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Warp kernel, 5 <= L <= 10.
+// ---------------------------------------------------------------------------
+template <int L>
+struct WarpShape {
+  static constexpr int T = Lay<L>::T;
+  static constexpr int VPW = 32 / T;                 // samples per warp step
+  static constexpr int R = VPW >= 8 ? 1 : 8 / VPW;   // steps per item
+  static constexpr int SPI = VPW * R;                // samples per item
+};
+
+template <int L, int MODE>
+__global__ void __launch_bounds__(kWarps * 32, 3) k_feat_warp(const Launch P) {
+  using Y = Lay<L>;
+  using WS = WarpShape<L>;
+  constexpr int d = Y::d;
+  __shared__ __align__(16) float sm[kWarps][WS::VPW * Y::SLOT];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / Y::T, lam = lane % Y::T;
+  float* buf = sm[warp];
+  const uint32_t buf_addr = smem_addr(buf);
+
+  const int E = P.a.E;
+  const int64_t tiles = (P.a.n + WS::SPI - 1) / WS::SPI;
+  const int64_t items = tiles * E;
+  const int64_t nw = (int64_t)gridDim.x * kWarps;
+  const int64_t wid = (int64_t)blockIdx.x * kWarps + warp;
+  const int64_t it0 = items * wid / nw, it1 = items * (wid + 1) / nw;
+
+  uint32_t bmask = 0;
+  float gt[32], cs[32];
+  uint32_t paddr[32];
+  int cur_e = -1;
+
+  for (int64_t it = it0; it < it1; ++it) {
+    // Features: expansion fastest (x rows of a tile reused from L1 across e).
+    // Logits: tile fastest (the expansion's slice of W stays in L1).
+    int64_t tile;
+    int e;
+    if constexpr (MODE == MODE_FEATURES) {
+      tile = it / E;
+      e = (int)(it % E);
+    } else {
+      e = (int)(it / tiles);
+      tile = it % tiles;
+    }
+    if (e != cur_e) {
+      cur_e = e;
+      const int64_t off = (int64_t)e * d;
+      bmask = load_bmask_A<L>(P.a.B_bits + (int64_t)e * (d / 32), lam);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int k = Y::kB(lam, j);
+        gt[j] = __ldg(P.a.G + off + k);
+        const uint32_t src = __ldg(P.a.perm + off + k);
+        paddr[j] = buf_addr + 4u * (uint32_t)spos<L>(g, (int)src);
+      }
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(P.a.Cs + off + Y::kA(lam, 4 * m)));
+        cs[4 * m] = v.x;
+        cs[4 * m + 1] = v.y;
+        cs[4 * m + 2] = v.z;
+        cs[4 * m + 3] = v.w;
+      }
+    }
+    for (int r = 0; r < WS::R; ++r) {
+      const int64_t n = tile * WS::SPI + r * WS::VPW + g;
+      const bool valid = n < P.a.n;
+      float w[32];
+      load_x_A<L>(P, n, valid, lam, w);
+      apply_signs(w, bmask);
+      // u = H B x-hat
+      hreg<Y::maskA()>(w);
+      if constexpr (L > 5) {
+        store_A<L>(buf, g, lam, w);
+        __syncwarp();
+        load_B<L>(buf, g, lam, w);
+      }
+      hreg<Y::maskB()>(w);
+      // v = Pi u: u goes to shared memory, each register gathers its source.
+      store_B<L>(buf, g, lam, w);
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < 32; ++j) w[j] = lds32(paddr[j]);
+      // h = H G v (G folded into the first butterfly stage)
+      hreg_scaled<Y::maskB()>(w, gt);
+      if constexpr (L > 5) {
+        __syncwarp();  // every lane finished gathering before the slots are reused
+        store_B<L>(buf, g, lam, w);
+        __syncwarp();
+        load_A<L>(buf, g, lam, w);
+      }
+      hreg<Y::maskA()>(w);
+      float acc[CMAX];
+#pragma unroll
+      for (int c = 0; c < CMAX; ++c) acc[c] = 0.f;
+      epilogue_A<L, MODE>(P, n, e, valid, lam, w, cs, acc);
+      if constexpr (MODE == MODE_LOGITS) {
+#pragma unroll
+        for (int c = 0; c < CMAX; ++c) {
+          float t = acc[c];
+#pragma unroll
+          for (int o = Y::T / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+          acc[c] = t;
+        }
+        if (valid && lam == 0) {
+          float* pr = P.part + (n * E + e) * P.C;
+#pragma unroll
+          for (int c = 0; c < CMAX; ++c)
+            if (c < P.C) pr[c] = acc[c];
+        }
+      }
+      if constexpr (L == 5) __syncwarp();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block kernel, 11 <= L <= 15: one block of T = 2^(L-5) threads per (n, e).
+// ---------------------------------------------------------------------------
+template <int L, int MODE>
+__global__ void __launch_bounds__(1 << (L - 5)) k_feat_cta(const Launch P) {
+  using Y = Lay<L>;
+  constexpr int d = Y::d, T = Y::T, NWARP = T / 32;
+  extern __shared__ float4 sm4[];
+  float* buf = reinterpret_cast<float*>(sm4);
+  __shared__ float red[NWARP][CMAX];
+  const uint32_t buf_addr = smem_addr(buf);
+  const int lam = threadIdx.x;
+  const int E = P.a.E;
+  const int64_t items = P.a.n * E;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int64_t n = it / E;
+    const int e = (int)(it % E);
+    const int64_t off = (int64_t)e * d;
+    float w[32];
+    load_x_A<L>(P, n, true, lam, w);
+    apply_signs(w, load_bmask_A<L>(P.a.B_bits + (int64_t)e * (d / 32), lam));
+    hreg<Y::maskA()>(w);
+    store_A<L>(buf, 0, lam, w);
+    __syncthreads();
+    load_B<L>(buf, 0, lam, w);
+    hreg<Y::maskB()>(w);
+    store_B<L>(buf, 0, lam, w);
+    __syncthreads();
+    load_C<L>(buf, lam, w);
+    hreg<Y::maskC()>(w);
+    store_C<L>(buf, lam, w);
+    __syncthreads();
+    // gather into layout C, then G and the C-phase of the second transform
+    float gt[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int k = Y::kC(lam, j);
+      const uint32_t src = __ldg(P.a.perm + off + k);
+      gt[j] = __ldg(P.a.G + off + k);
+      w[j] = lds32(buf_addr + 4u * (uint32_t)spos<L>(0, (int)src));
+    }
+    hreg_scaled<Y::maskC()>(w, gt);
+    __syncthreads();
+    store_C<L>(buf, lam, w);
+    __syncthreads();
+    load_B<L>(buf, 0, lam, w);
+    hreg<Y::maskB()>(w);
+    store_B<L>(buf, 0, lam, w);
+    __syncthreads();
+    load_A<L>(buf, 0, lam, w);
+    hreg<Y::maskA()>(w);
+    float cs[32];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(P.a.Cs + off + Y::kA(lam, 4 * m)));
+      cs[4 * m] = v.x;
+      cs[4 * m + 1] = v.y;
+      cs[4 * m + 2] = v.z;
+      cs[4 * m + 3] = v.w;
+    }
+    float acc[CMAX];
+#pragma unroll
+    for (int c = 0; c < CMAX; ++c) acc[c] = 0.f;
+    epilogue_A<L, MODE>(P, n, e, true, lam, w, cs, acc);
+    if constexpr (MODE == MODE_LOGITS) {
+#pragma unroll
+      for (int c = 0; c < CMAX; ++c) {
+        float t = acc[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if ((lam & 31) == 0) red[lam >> 5][c] = t;
+      }
+      __syncthreads();
+      if (lam < P.C) {
+        float t = 0.f;
+        for (int q = 0; q < NWARP; ++q) t += red[q][lam];
+        P.part[(n * E + e) * P.C + lam] = t;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Thread kernel, 1 <= L <= 4: one thread per (n, e), everything in registers.
+// ---------------------------------------------------------------------------
+template <int L>
+__device__ __forceinline__ void hsmall(float (&w)[1 << L]) {
+#pragma unroll
+  for (int h = 1; h < (1 << L); h <<= 1)
+#pragma unroll
+    for (int k = 0; k < (1 << L); ++k)
+      if (!(k & h)) {
+        const float a = w[k], c = w[k | h];
+        w[k] = a + c;
+        w[k | h] = a - c;
+      }
+}
+
+template <int L, int MODE>
+__global__ void __launch_bounds__(128) k_feat_tiny(const Launch P) {
+  constexpr int d = 1 << L;
+  const int E = P.a.E;
+  const int64_t items = P.a.n * E;
+  const int64_t F = 2ll * E * d;
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < items;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = it / E;
+    const int e = (int)(it % E);
+    const int64_t off = (int64_t)e * d;
+    const float* row = P.a.x + n * P.a.ldx;
+    const uint32_t bits = __ldg(P.a.B_bits + e);
+    float u[d], w[d];
+#pragma unroll
+    for (int k = 0; k < d; ++k) {
+      const float xv = (k < P.a.in_dim) ? __ldg(row + k) : 0.f;
+      u[k] = (bits >> k & 1u) ? -xv : xv;
+    }
+    hsmall<L>(u);
+#pragma unroll
+    for (int k = 0; k < d; ++k) {
+      const uint32_t src = __ldg(P.a.perm + off + k);
+      float v = 0.f;
+#pragma unroll
+      for (int q = 0; q < d; ++q) v = (src == (uint32_t)q) ? u[q] : v;  // register select, no local memory
+      w[k] = __ldg(P.a.G + off + k) * v;
+    }
+    hsmall<L>(w);
+    float acc[CMAX];
+#pragma unroll
+    for (int c = 0; c < CMAX; ++c) acc[c] = 0.f;
+#pragma unroll
+    for (int k = 0; k < d; ++k) {
+      float c, s;
+      cos_sin(__ldg(P.a.Cs + off + k) * w[k], c, s);
+      if constexpr (MODE == MODE_FEATURES) {
+        P.phi[n * F + 2ll * e * d + k] = c;
+        P.phi[n * F + 2ll * e * d + d + k] = s;
+      } else {
+        for (int cl = 0; cl < P.C; ++cl) {
+          const float* wr = P.W + cl * F + 2ll * e * d;
+          acc[cl] = fmaf(__ldg(wr + k), c, fmaf(__ldg(wr + d + k), s, acc[cl]));
+        }
+      }
+    }
+    if constexpr (MODE == MODE_LOGITS) {
+      for (int cl = 0; cl < P.C; ++cl) P.part[(n * E + e) * P.C + cl] = acc[cl];
+    }
+  }
+}
+
+// logits[n][c] = b[c] + sum_e part[n][e][c], expansions summed in order.
+__global__ void k_logits_reduce(const float* __restrict__ part, const float* __restrict__ b,
+                                int64_t n, int E, int C, float* __restrict__ logits) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * C) return;
+  const int64_t i = t / C;
+  const int c = (int)(t % C);
+  float s = 0.f;
+  for (int e = 0; e < E; ++e) s += part[(i * E + e) * C + c];
+  logits[t] = s + (b ? b[c] : 0.f);
+}
+
+template <class K>
+int occ_blocks(K kernel, int threads, size_t smem) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem) != cudaSuccess)
+    b = 1;
+  return std::max(b, 1);
+}
+
+template <int L, int MODE>
+cudaError_t run(const Launch& P, cudaStream_t s) {
+  const int num_sms = P.a.num_sms;
+  if constexpr (L <= 4) {
+    const int occ = occ_blocks(k_feat_tiny<L, MODE>, 128, 0);
+    const int64_t need = (P.a.n * P.a.E + 127) / 128;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms * occ));
+    k_feat_tiny<L, MODE><<<grid, 128, 0, s>>>(P);
+  } else if constexpr (L <= 10) {
+    const int occ = occ_blocks(k_feat_warp<L, MODE>, kWarps * 32, 0);
+    const int64_t items = (P.a.n + WarpShape<L>::SPI - 1) / WarpShape<L>::SPI * P.a.E;
+    const int64_t need = (items + kWarps - 1) / kWarps;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms * occ));
+    k_feat_warp<L, MODE><<<grid, kWarps * 32, 0, s>>>(P);
+  } else {
+    const size_t smem = sizeof(float) * Lay<L>::SLOT;
+    cudaError_t err = cudaFuncSetAttribute(k_feat_cta<L, MODE>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    const int occ = occ_blocks(k_feat_cta<L, MODE>, Lay<L>::T, smem);
+    const int64_t items = P.a.n * P.a.E;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)num_sms * occ));
+    k_feat_cta<L, MODE><<<grid, Lay<L>::T, smem, s>>>(P);
+  }
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t dispatch(const Launch& P, cudaStream_t s) {
+  switch (P.a.L) {
+    case 1: return run<1, MODE>(P, s);
+    case 2: return run<2, MODE>(P, s);
+    case 3: return run<3, MODE>(P, s);
+    case 4: return run<4, MODE>(P, s);
+    case 5: return run<5, MODE>(P, s);
+    case 6: return run<6, MODE>(P, s);
+    case 7: return run<7, MODE>(P, s);
+    case 8: return run<8, MODE>(P, s);
+    case 9: return run<9, MODE>(P, s);
+    case 10: return run<10, MODE>(P, s);
+    case 11: return run<11, MODE>(P, s);
+    case 12: return run<12, MODE>(P, s);
+    case 13: return run<13, MODE>(P, s);
+    case 14: return run<14, MODE>(P, s);
+    case 15: return run<15, MODE>(P, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+Launch make_launch(const FeatureArgs& a) {
+  Launch P{};
+  P.a = a;
+  P.vec_x = (a.in_dim % 4 == 0) && (a.ldx % 4 == 0) &&
+            (reinterpret_cast<uintptr_t>(a.x) % 16 == 0);
+  return P;
+}
+
+}  // namespace
+
+cudaError_t launch_features(const FeatureArgs& a, float* phi, cudaStream_t s) {
+  if (a.n == 0) return cudaSuccess;
+  Launch P = make_launch(a);
+  P.phi = phi;
+  return dispatch<MODE_FEATURES>(P, s);
+}
+
+cudaError_t launch_logits(const FeatureArgs& a, const float* W, const float* b, int C,
+                          float* part, float* logits, cudaStream_t s) {
+  if (a.n == 0) return cudaSuccess;
+  Launch P = make_launch(a);
+  P.W = W;
+  P.part = part;
+  P.C = C;
+  cudaError_t err = dispatch<MODE_LOGITS>(P, s);
+  if (err != cudaSuccess) return err;
+  const int64_t total = a.n * C;
+  k_logits_reduce<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(part, b, a.n, a.E, C, logits);
+  return cudaGetLastError();
+}
+
+}  // namespace mck

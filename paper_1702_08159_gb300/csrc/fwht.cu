@@ -1,0 +1,248 @@
+// Standalone batched in-place unnormalised Walsh-Hadamard transform
+// (Sec. "Fast Walsh Hadamard"; the paper's Sec. "Implementation of Fast Walsh
+// Hadamard" splits a large transform into passes over memory down to an
+// in-cache routine -- here the "cache" is registers plus shared memory).
+//
+// Regimes, by L = log2 d:
+//   L = 1..4    one thread per vector, entirely in registers.
+//   L = 5..10   a group of 2^(L-5) lanes per vector (32/2^(L-5) vectors per
+//               warp): register phases A and B with one shared-memory layout
+//               move in between, 128-bit coalesced global loads and stores.
+//   L = 11..15  one block of 2^(L-5) threads per vector: phases A, B, C.
+//   L = 16..20  two passes over HBM: the L = 15 kernel on every 2^15 block
+//               (index bits 0..14), then a column pass over bits 15..L-1.
+// Every element is read and written once per pass.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace mck {
+namespace {
+
+constexpr int kWarpsPerBlock = 4;
+
+template <int L>
+__global__ void __launch_bounds__(128) k_fwht_tiny(float* __restrict__ x, int64_t n) {
+  constexpr int d = 1 << L;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    float w[d];
+    float* p = x + v * d;
+#pragma unroll
+    for (int k = 0; k < d; ++k) w[k] = p[k];
+#pragma unroll
+    for (int h = 1; h < d; h <<= 1)
+#pragma unroll
+      for (int k = 0; k < d; ++k)
+        if (!(k & h)) {
+          const float a = w[k], c = w[k | h];
+          w[k] = a + c;
+          w[k | h] = a - c;
+        }
+#pragma unroll
+    for (int k = 0; k < d; ++k) p[k] = w[k];
+  }
+}
+
+template <int L>
+__device__ __forceinline__ void gload_A(const float* __restrict__ row, int lam, bool valid,
+                                        float (&w)[32]) {
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) v = __ldcs(reinterpret_cast<const float4*>(row + Lay<L>::kA(lam, 4 * m)));
+    w[4 * m] = v.x;
+    w[4 * m + 1] = v.y;
+    w[4 * m + 2] = v.z;
+    w[4 * m + 3] = v.w;
+  }
+}
+
+template <int L>
+__device__ __forceinline__ void gstore_A(float* __restrict__ row, int lam, const float (&w)[32]) {
+#pragma unroll
+  for (int m = 0; m < 8; ++m)
+    __stcs(reinterpret_cast<float4*>(row + Lay<L>::kA(lam, 4 * m)),
+           make_float4(w[4 * m], w[4 * m + 1], w[4 * m + 2], w[4 * m + 3]));
+}
+
+template <int L>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_fwht_warp(float* __restrict__ x,
+                                                                    int64_t n) {
+  using Y = Lay<L>;
+  constexpr int VPW = 32 / Y::T;
+  __shared__ __align__(16) float sm[kWarpsPerBlock][VPW * Y::SLOT];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / Y::T, lam = lane % Y::T;
+  float* buf = sm[warp];
+  const int64_t groups = (n + VPW - 1) / VPW;
+  for (int64_t grp = (int64_t)blockIdx.x * kWarpsPerBlock + warp; grp < groups;
+       grp += (int64_t)gridDim.x * kWarpsPerBlock) {
+    const int64_t v = grp * VPW + g;
+    const bool valid = v < n;
+    float* row = x + v * Y::d;
+    float w[32];
+    gload_A<L>(row, lam, valid, w);
+    hreg<Y::maskA()>(w);
+    if constexpr (L > 5) {
+      store_A<L>(buf, g, lam, w);
+      __syncwarp();
+      load_B<L>(buf, g, lam, w);
+    }
+    hreg<Y::maskB()>(w);
+    if constexpr (L > 5) {
+      // A thread rewrites exactly the slots it just read, so no barrier is
+      // needed between a load phase and the next store phase.
+      store_B<L>(buf, g, lam, w);
+      __syncwarp();
+      load_A<L>(buf, g, lam, w);
+    }
+    if (valid) gstore_A<L>(row, lam, w);
+  }
+}
+
+// One block per vector of 2^L (11 <= L <= 15); blocks stride over vectors.
+template <int L>
+__global__ void __launch_bounds__(1 << (L - 5)) k_fwht_cta(float* __restrict__ x, int64_t n) {
+  using Y = Lay<L>;
+  extern __shared__ float4 sm4[];
+  float* buf = reinterpret_cast<float*>(sm4);
+  const int lam = threadIdx.x;
+  for (int64_t v = blockIdx.x; v < n; v += gridDim.x) {
+    float* row = x + v * Y::d;
+    float w[32];
+    gload_A<L>(row, lam, true, w);
+    hreg<Y::maskA()>(w);
+    // Barriers only between a store phase and the next load phase: a thread
+    // rewrites exactly the slots it read, so loads need no trailing barrier.
+    store_A<L>(buf, 0, lam, w);
+    __syncthreads();
+    load_B<L>(buf, 0, lam, w);
+    hreg<Y::maskB()>(w);
+    store_B<L>(buf, 0, lam, w);
+    __syncthreads();
+    load_C<L>(buf, lam, w);
+    hreg<Y::maskC()>(w);
+    store_C<L>(buf, lam, w);
+    __syncthreads();
+    load_A<L>(buf, 0, lam, w);
+    gstore_A<L>(row, lam, w);
+  }
+}
+
+// Column pass of the two-pass regime: H over index bits 15..L-1 of each
+// vector. Thread t of vector v handles column c = t (mod 2^15): the R = 2^(L-15)
+// elements c + 2^15 i, i < R, kept in registers. Consecutive threads read
+// consecutive columns (coalesced).
+template <int R>
+__global__ void __launch_bounds__(256) k_fwht_columns(float* __restrict__ x, int64_t n) {
+  constexpr int64_t kBlock = 1 << 15;
+  const int64_t total = n * kBlock;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = t / kBlock, c = t % kBlock;
+    float* p = x + v * kBlock * R + c;
+    float w[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) w[i] = __ldcs(p + i * kBlock);
+#pragma unroll
+    for (int h = 1; h < R; h <<= 1)
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+        if (!(i & h)) {
+          const float a = w[i], b = w[i | h];
+          w[i] = a + b;
+          w[i | h] = a - b;
+        }
+#pragma unroll
+    for (int i = 0; i < R; ++i) __stcs(p + i * kBlock, w[i]);
+  }
+}
+
+template <class K>
+int occupancy_blocks(K kernel, int threads, size_t smem) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem) != cudaSuccess)
+    b = 1;
+  return std::max(b, 1);
+}
+
+inline unsigned grid_for(int64_t work, int per_block, int num_sms, int occ) {
+  const int64_t need = (work + per_block - 1) / per_block;
+  const int64_t cap = (int64_t)num_sms * occ;
+  return (unsigned)std::max<int64_t>(1, std::min(need, cap));
+}
+
+template <int L>
+cudaError_t run_tiny(float* x, int64_t n, int num_sms, cudaStream_t s) {
+  const int occ = occupancy_blocks(k_fwht_tiny<L>, 128, 0);
+  k_fwht_tiny<L><<<grid_for(n, 128, num_sms, occ), 128, 0, s>>>(x, n);
+  return cudaGetLastError();
+}
+
+template <int L>
+cudaError_t run_warp(float* x, int64_t n, int num_sms, cudaStream_t s) {
+  constexpr int VPW = 32 / Lay<L>::T;
+  const int occ = occupancy_blocks(k_fwht_warp<L>, kWarpsPerBlock * 32, 0);
+  k_fwht_warp<L><<<grid_for(n, VPW * kWarpsPerBlock, num_sms, occ), kWarpsPerBlock * 32, 0,
+                   s>>>(x, n);
+  return cudaGetLastError();
+}
+
+template <int L>
+cudaError_t run_cta(float* x, int64_t n, int num_sms, cudaStream_t s) {
+  const size_t smem = sizeof(float) * Lay<L>::SLOT;
+  cudaError_t err =
+      cudaFuncSetAttribute(k_fwht_cta<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  const int occ = occupancy_blocks(k_fwht_cta<L>, Lay<L>::T, smem);
+  k_fwht_cta<L><<<grid_for(n, 1, num_sms, occ), Lay<L>::T, smem, s>>>(x, n);
+  return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t run_columns(float* x, int64_t n, int num_sms, cudaStream_t s) {
+  const int occ = occupancy_blocks(k_fwht_columns<R>, 256, 0);
+  k_fwht_columns<R><<<grid_for(n << 15, 256, num_sms, occ), 256, 0, s>>>(x, n);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_fwht(float* x, int64_t n, int L, int num_sms, cudaStream_t s) {
+  if (n == 0 || L == 0) return cudaSuccess;
+  switch (L) {
+    case 1: return run_tiny<1>(x, n, num_sms, s);
+    case 2: return run_tiny<2>(x, n, num_sms, s);
+    case 3: return run_tiny<3>(x, n, num_sms, s);
+    case 4: return run_tiny<4>(x, n, num_sms, s);
+    case 5: return run_warp<5>(x, n, num_sms, s);
+    case 6: return run_warp<6>(x, n, num_sms, s);
+    case 7: return run_warp<7>(x, n, num_sms, s);
+    case 8: return run_warp<8>(x, n, num_sms, s);
+    case 9: return run_warp<9>(x, n, num_sms, s);
+    case 10: return run_warp<10>(x, n, num_sms, s);
+    case 11: return run_cta<11>(x, n, num_sms, s);
+    case 12: return run_cta<12>(x, n, num_sms, s);
+    case 13: return run_cta<13>(x, n, num_sms, s);
+    case 14: return run_cta<14>(x, n, num_sms, s);
+    case 15: return run_cta<15>(x, n, num_sms, s);
+    default: break;
+  }
+  if (L > 20) return cudaErrorInvalidValue;
+  const int64_t blocks = n << (L - 15);
+  cudaError_t err = run_cta<15>(x, blocks, num_sms, s);
+  if (err != cudaSuccess) return err;
+  switch (L) {
+    case 16: return run_columns<2>(x, n, num_sms, s);
+    case 17: return run_columns<4>(x, n, num_sms, s);
+    case 18: return run_columns<8>(x, n, num_sms, s);
+    case 19: return run_columns<16>(x, n, num_sms, s);
+    default: return run_columns<32>(x, n, num_sms, s);
+  }
+}
+
+}  // namespace mck

@@ -1,0 +1,81 @@
+// Private interface between the C-ABI layer (api.cu) and the kernel files.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/mck.h"
+
+struct mck_plan_s {
+  int64_t d = 0;
+  int L = 0;  // log2(d)
+  int32_t E = 0;
+  int32_t kernel = 0;
+  double sigma = 0.0;
+  int32_t matern_t = 0;
+  uint64_t seed = 0;
+  int device = 0;
+  int num_sms = 0;
+  // Device tables (natural order, see mck_plan_tables).
+  uint32_t* B_bits = nullptr;  // E x words
+  uint32_t* perm = nullptr;    // E x d
+  float* G = nullptr;          // E x d
+  float* Cs = nullptr;         // E x d
+  int64_t words = 0;           // ceil(d / 32)
+};
+
+namespace mck {
+
+// Thread-local error message; returns the status for convenient `return fail(...)`.
+mck_status_t fail(mck_status_t s, const std::string& msg);
+mck_status_t cuda_fail(cudaError_t err, const char* where);
+
+// ---- plan.cu -------------------------------------------------------------
+mck_status_t build_tables(mck_plan_s* p, cudaStream_t s);
+
+// ---- fwht.cu -------------------------------------------------------------
+cudaError_t launch_fwht(float* x, int64_t n, int L, int num_sms, cudaStream_t s);
+
+// ---- features.cu -----------------------------------------------------------
+struct FeatureArgs {
+  const float* x;
+  int64_t n;
+  int64_t in_dim;
+  int64_t ldx;
+  const uint32_t* B_bits;
+  const uint32_t* perm;
+  const float* G;
+  const float* Cs;
+  int32_t E;
+  int L;
+  int num_sms;
+};
+
+cudaError_t launch_features(const FeatureArgs& a, float* phi, cudaStream_t s);
+// Partial logits per (sample, expansion): part is n x E x C; then logits = sum_e part + b.
+cudaError_t launch_logits(const FeatureArgs& a, const float* W, const float* b, int C,
+                          float* part, float* logits, cudaStream_t s);
+
+// ---- train.cu ------------------------------------------------------------
+cudaError_t launch_softmax_xent(const float* logits, const int32_t* labels, int64_t n, int C,
+                                float* loss, float* dlogits, cudaStream_t s);
+
+struct BackwardArgs {
+  FeatureArgs f;
+  const float* dphi;     // n x 2Ed, or null when dlogits/W are given
+  const float* W;        // C x 2Ed (fused logits backward)
+  const float* dlogits;  // n x C
+  int C;
+  float* phi_out;  // optional n x 2Ed: recomputed features (for dW)
+  float* dx;
+  float* dCs;
+  float* dG;
+};
+// partials: num_partials x 2 x d floats, num_partials = E x (warps per expansion).
+cudaError_t launch_backward(const BackwardArgs& a, float* partials, int64_t num_partials,
+                            cudaStream_t s);
+cudaError_t launch_logit_weight_grads(const float* dlogits, const float* phi, int64_t n, int C,
+                                      int64_t F, float* dW, float* db, cudaStream_t s);
+
+}  // namespace mck

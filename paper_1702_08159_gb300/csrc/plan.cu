@@ -1,0 +1,264 @@
+// Plan-time table generation: B, Pi, G and the calibration C of E expansions,
+// all recreated from the seed with Philox4x32-10 (Sec. "McKernel": B from
+// hash bits, Pi by Fisher-Yates driven by the hash, G by Box-Muller driven by
+// the hash, C kernel-dependent; Sec. "API Description": nothing is stored).
+//
+// Counter layout (c0, c1, c2, c3) = (index, expansion, tag, sub-draw); key =
+// the 64-bit seed as two words. This file is compiled with --fmad=false so
+// that the double-precision formulas round exactly as written (G and the RBF
+// radius then match an IEEE float64 evaluation of the same formulas up to the
+// last-place differences of log/cos).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "internal.h"
+#include "philox.cuh"
+
+namespace mck {
+namespace {
+
+constexpr double kTwoM32 = 2.3283064365386962890625e-10;  // 2^-32
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+__device__ __forceinline__ double unit_open0(uint32_t w) { return ((double)w + 1.0) * kTwoM32; }
+__device__ __forceinline__ double unit_closed0(uint32_t w) { return (double)w * kTwoM32; }
+
+// Box-Muller (1958), cosine branch: sqrt(-2 ln u1) cos(2 pi u2).
+__device__ __forceinline__ double box_muller_cos(uint32_t w0, uint32_t w1) {
+  const double r = sqrt(-2.0 * log(unit_open0(w0)));
+  const double a = 2.0 * kPi * unit_closed0(w1);
+  return r * cos(a);
+}
+
+// B: bit (k mod 32) of word k/32 set where B_e[k] = -1 (bit 0 of Philox word 0).
+__global__ void k_plan_B(uint32_t* __restrict__ bits, int64_t d, int64_t words, int32_t E,
+                         uint32_t k0, uint32_t k1) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= words * E) return;
+  const uint32_t e = (uint32_t)(t / words);
+  const int64_t w = t % words;
+  uint32_t out = 0;
+  for (int b = 0; b < 32; ++b) {
+    const int64_t k = 32 * w + b;
+    if (k < d) out |= (philox4x32_10((uint32_t)k, e, kTagB, 0, k0, k1).x & 1u) << b;
+  }
+  bits[t] = out;
+}
+
+// G_e[k] (float table) and its float64 value (for ||G_e||).
+__global__ void k_plan_G(float* __restrict__ G, double* __restrict__ G64, int64_t d, int32_t E,
+                         uint32_t k0, uint32_t k1) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d * E) return;
+  const uint32_t e = (uint32_t)(t / d), k = (uint32_t)(t % d);
+  const U32x4 w = philox4x32_10(k, e, kTagG, 0, k0, k1);
+  const double g = box_muller_cos(w.x, w.y);
+  G64[t] = g;
+  G[t] = (float)g;
+}
+
+// ||G_e||_2 in float64, one block per expansion (fixed summation order).
+__global__ void k_plan_norm(const double* __restrict__ G64, double* __restrict__ norm, int64_t d) {
+  __shared__ double part[1024];
+  const double* g = G64 + (int64_t)blockIdx.x * d;
+  double s = 0.0;
+  for (int64_t k = threadIdx.x; k < d; k += blockDim.x) s += g[k] * g[k];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) norm[blockIdx.x] = sqrt(part[0]);
+}
+
+// RBF radius r ~ chi_d: r^2 = 2 Gamma(d/2, 1) by Marsaglia & Tsang (2000):
+// dd = d/2 - 1/3, c = 1/sqrt(9 dd); trial j draws g ~ N(0,1) (words 0, 1) and
+// U (word 2) from counter (k, e, 4, j); v = (1 + c g)^3 > 0 is accepted when
+// ln U < g^2/2 + dd - dd v + dd ln v; then r^2 = 2 dd v. Cs = r/||G_e||/(sigma sqrt d).
+__global__ void k_plan_rbf(float* __restrict__ Cs, const double* __restrict__ norm, int64_t d,
+                           int32_t E, double inv_sigma_sqrt_d, uint32_t k0, uint32_t k1) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d * E) return;
+  const uint32_t e = (uint32_t)(t / d), k = (uint32_t)(t % d);
+  const double a = (double)d / 2.0;
+  const double dd = a - 1.0 / 3.0;
+  const double c = 1.0 / sqrt(9.0 * dd);
+  double r = 0.0;
+  for (uint32_t j = 0; j < 64; ++j) {
+    const U32x4 w = philox4x32_10(k, e, kTagRbf, j, k0, k1);
+    const double g = box_muller_cos(w.x, w.y);
+    const double u = unit_open0(w.z);
+    double v = 1.0 + c * g;
+    if (v <= 0.0) continue;
+    v = v * v * v;
+    if (log(u) < 0.5 * g * g + dd - dd * v + dd * log(v)) {
+      r = sqrt(2.0 * dd * v);
+      break;
+    }
+  }
+  Cs[t] = (float)((r / norm[e]) * inv_sigma_sqrt_d);
+}
+
+// Matern radius (Sec. "Customizing McKernel"): r = || sum_{j=1..t} u_j || with
+// u_j = U_j^{1/d} X_j/||X_j||, X_j ~ N(0, I_d) (coordinates 2p, 2p+1 are the
+// Box-Muller pair of counter (p, e, 5 + 16k, j)), U_j = (w0+1)/2^32 of
+// counter (k, e, 6, j). One block per (e, k) (block index e*d + k); each thread owns up to 16 pairs
+// of coordinates of the running sum. X_j is drawn twice (once for its norm,
+// once to accumulate), which keeps the sum in registers. Float32 coordinates,
+// float64 norms.
+constexpr int kBallPairs = 16;
+
+__global__ void __launch_bounds__(1024) k_plan_matern(float* __restrict__ Cs,
+                                                      const double* __restrict__ norm, int64_t d,
+                                                      int32_t t_order, double inv_sigma_sqrt_d,
+                                                      uint32_t k0, uint32_t k1) {
+  __shared__ double red[32];
+  __shared__ double bcast;
+  const int64_t pairs = d / 2;
+  const uint32_t e = (uint32_t)(blockIdx.x / d), k = (uint32_t)(blockIdx.x % d);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  float s[2 * kBallPairs];
+#pragma unroll
+  for (int i = 0; i < 2 * kBallPairs; ++i) s[i] = 0.f;
+
+  auto block_sum = [&](double v) -> double {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid < 32) {
+      double x = (tid < (nt + 31) / 32) ? red[tid] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (tid == 0) bcast = x;
+    }
+    __syncthreads();
+    const double out = bcast;
+    __syncthreads();
+    return out;
+  };
+
+  auto coords = [&](int64_t p, uint32_t j, float& xc, float& xs) {
+    const U32x4 w = philox4x32_10((uint32_t)p, e, kTagBall + 16u * k, j, k0, k1);
+    const float u1 = (float)(((double)w.x + 1.0) * kTwoM32);
+    const float u2 = (float)((double)w.y * kTwoM32);
+    const float r = sqrtf(-2.0f * logf(u1));
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);
+    xc = r * cs;
+    xs = r * sn;
+  };
+
+  for (uint32_t j = 1; j <= (uint32_t)t_order; ++j) {
+    double ss = 0.0;
+#pragma unroll
+    for (int i = 0; i < kBallPairs; ++i) {
+      const int64_t p = tid + (int64_t)i * nt;
+      if (p < pairs) {
+        float xc, xs;
+        coords(p, j, xc, xs);
+        ss += (double)xc * xc + (double)xs * xs;
+      }
+    }
+    const double xnorm = sqrt(block_sum(ss));
+    const U32x4 wr = philox4x32_10(k, e, kTagBallRadius, j, k0, k1);
+    const double rho = pow(unit_open0(wr.x), 1.0 / (double)d);
+    const float scale = (float)(rho / xnorm);
+#pragma unroll
+    for (int i = 0; i < kBallPairs; ++i) {
+      const int64_t p = tid + (int64_t)i * nt;
+      if (p < pairs) {
+        float xc, xs;
+        coords(p, j, xc, xs);
+        s[2 * i] = fmaf(scale, xc, s[2 * i]);
+        s[2 * i + 1] = fmaf(scale, xs, s[2 * i + 1]);
+      }
+    }
+  }
+  double ss = 0.0;
+#pragma unroll
+  for (int i = 0; i < kBallPairs; ++i) {
+    const int64_t p = tid + (int64_t)i * nt;
+    if (p < pairs) ss += (double)s[2 * i] * s[2 * i] + (double)s[2 * i + 1] * s[2 * i + 1];
+  }
+  const double r = sqrt(block_sum(ss));
+  if (tid == 0) Cs[(int64_t)e * d + k] = (float)((r / norm[e]) * inv_sigma_sqrt_d);
+}
+
+// Pi_e by Durstenfeld's Fisher-Yates on L = [0..d-1]: for i = d-1 down to 1,
+// j = floor(w0 (i+1) / 2^32) from counter (i, e, 2, 0), swap L[i], L[j].
+// One block per expansion: the draws of 1024 consecutive steps are computed
+// in parallel, then one thread applies the swaps in order (the shuffle is
+// sequential by definition). L lives in shared memory (d <= 2^15).
+__global__ void k_plan_perm(uint32_t* __restrict__ perm, int64_t d, uint32_t k0, uint32_t k1) {
+  extern __shared__ uint32_t sm[];
+  uint32_t* Ls = sm;
+  uint32_t* J = sm + d;
+  const uint32_t e = blockIdx.x;
+  for (int64_t i = threadIdx.x; i < d; i += blockDim.x) Ls[i] = (uint32_t)i;
+  __syncthreads();
+  for (int64_t hi = d - 1; hi >= 1; hi -= 1024) {
+    const int64_t lo = hi - 1023 > 1 ? hi - 1023 : 1;
+    for (int64_t i = lo + threadIdx.x; i <= hi; i += blockDim.x) {
+      const U32x4 w = philox4x32_10((uint32_t)i, e, kTagPerm, 0, k0, k1);
+      J[i - lo] = __umulhi(w.x, (uint32_t)(i + 1));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int64_t i = hi; i >= lo; --i) {
+        const uint32_t j = J[i - lo];
+        const uint32_t a = Ls[i];
+        Ls[i] = Ls[j];
+        Ls[j] = a;
+      }
+    }
+    __syncthreads();
+  }
+  for (int64_t i = threadIdx.x; i < d; i += blockDim.x) perm[(int64_t)e * d + i] = Ls[i];
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+mck_status_t build_tables(mck_plan_s* p, cudaStream_t s) {
+  const uint32_t k0 = (uint32_t)(p->seed & 0xffffffffu), k1 = (uint32_t)(p->seed >> 32);
+  const int64_t d = p->d, E = p->E, n = d * E;
+  double* G64 = nullptr;
+  double* norm = nullptr;
+  cudaError_t err = cudaMallocAsync(&G64, sizeof(double) * n, s);
+  if (err == cudaSuccess) err = cudaMallocAsync(&norm, sizeof(double) * E, s);
+  if (err != cudaSuccess) {
+    if (G64) cudaFreeAsync(G64, s);
+    cudaGetLastError();
+    return fail(MCK_ENOMEM, "plan: scratch allocation failed");
+  }
+  k_plan_B<<<blocks_for(p->words * E, 256), 256, 0, s>>>(p->B_bits, d, p->words, p->E, k0, k1);
+  k_plan_G<<<blocks_for(n, 256), 256, 0, s>>>(p->G, G64, d, p->E, k0, k1);
+  k_plan_norm<<<(unsigned)E, 1024, 0, s>>>(G64, norm, d);
+  const double inv = 1.0 / (p->sigma * std::sqrt((double)d));
+  if (p->kernel == MCK_RBF) {
+    k_plan_rbf<<<blocks_for(n, 128), 128, 0, s>>>(p->Cs, norm, d, p->E, inv, k0, k1);
+  } else {
+    const int64_t pairs = d / 2;
+    int threads = (int)((pairs + kBallPairs - 1) / kBallPairs);
+    threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : threads);
+    k_plan_matern<<<(unsigned)(d * E), threads, 0, s>>>(p->Cs, norm, d, p->matern_t, inv, k0, k1);
+  }
+  const size_t perm_smem = sizeof(uint32_t) * (size_t)(d + 1024);
+  err = cudaFuncSetAttribute(k_plan_perm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)perm_smem);
+  if (err == cudaSuccess) {
+    k_plan_perm<<<(unsigned)E, 1024, perm_smem, s>>>(p->perm, d, k0, k1);
+    err = cudaGetLastError();
+  }
+  cudaFreeAsync(G64, s);
+  cudaFreeAsync(norm, s);
+  if (err != cudaSuccess) return cuda_fail(err, "plan kernels");
+  err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return cuda_fail(err, "plan kernels");
+  return MCK_OK;
+}
+
+}  // namespace mck

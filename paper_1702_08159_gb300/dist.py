@@ -1,0 +1,46 @@
+"""Data-parallel helpers for running the feature map on several GPUs.
+
+Samples are independent and every rank rebuilds the same tables from the
+seed (Sec. "Large-scale Machine Learning": hashing makes the parameters
+reproducible anywhere, which "is crucial for distributed computation"), so
+inference shards the batch with no collective at all. Training would sum
+gradients across ranks (``allreduce_grads``).
+"""
+
+import torch
+import torch.distributed as dist
+
+
+def shard_range(n, rank, world):
+    """Contiguous [lo, hi) of n samples for `rank`; shards differ by at most one sample."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("need 0 <= rank < world")
+    base, extra = divmod(n, world)
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
+def max_over_ranks(value, device=None):
+    """The maximum of a float over all ranks (a single rank returns it unchanged)."""
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value, device=None):
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def allreduce_grads(params):
+    """Sum the gradients of `params` over ranks, in place (data-parallel training)."""
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return
+    for p in params:
+        if p.grad is not None:
+            dist.all_reduce(p.grad, op=dist.ReduceOp.SUM)

@@ -26,3 +26,26 @@ def read_golden(name):
 @pytest.fixture(scope="session")
 def golden():
     return read_golden
+
+
+@pytest.fixture(scope="session")
+def mck():
+    """The CUDA binding with libmck.so built for this machine (GPU tests only)."""
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1702_08159_gb300 import build
+
+    build.build()
+    import paper_1702_08159_gb300 as m
+
+    torch.cuda.set_device(0)
+    return m
+
+
+@pytest.fixture(scope="session")
+def dev():
+    import torch
+
+    return torch.device("cuda", 0)

@@ -1,0 +1,143 @@
+"""Fused feature kernel (mck_features) against the FP64 oracle.
+
+Bar: max abs error <= 1e-5 on every feature (float32 path vs float64 oracle).
+Sizes span the three kernels (thread: d <= 16, warp: 32 <= d <= 1024, block:
+2048 <= d <= 32768), ragged batches, ragged and strided inputs, learned
+(overridden) C and G, both calibrations, and the full-size workloads on
+sampled rows.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as wl
+from oracle import fastfood as ff
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def _oracle_tables(plan):
+    return ff.plan_tables(plan.d, plan.E, plan.kernel, plan.sigma, t=plan.matern_t or 40,
+                          seed=plan.seed)
+
+
+def _max_err(got, ref):
+    return float(np.abs(got.astype(np.float64) - ref).max())
+
+
+def test_config0_full(mck, dev):
+    # N=256 MNIST-shaped rows (784 -> 1024), E=1, sigma=1, RBF, seed 42.
+    plan = mck.Plan(1024, 1, "rbf", 1.0, 42)
+    x = wl.mnist_like(256, 784, seed=42)
+    phi = mck.features(plan, torch.from_numpy(x).to(dev)).cpu().numpy()
+    assert phi.shape == (256, 2048)
+    ref = ff.features(x.astype(np.float64), _oracle_tables(plan))
+    assert _max_err(phi, ref) <= TOL
+
+
+@pytest.mark.parametrize("L", list(range(1, 16)))
+def test_all_sizes(mck, dev, L):
+    d = 1 << L
+    E = 2 if L < 14 else 1
+    n = 9 if L <= 12 else 3
+    plan = mck.Plan(d, E, "rbf", 2.0, 1000 + L)
+    in_dim = max(1, d - d // 4)
+    x = wl.gaussian(n, in_dim, seed=L) * np.float32(0.5)
+    phi = mck.features(plan, torch.from_numpy(x).to(dev)).cpu().numpy()
+    ref = ff.features(x.astype(np.float64), _oracle_tables(plan))
+    assert _max_err(phi, ref) <= TOL
+
+
+@pytest.mark.parametrize("in_dim", [1, 3, 783, 784, 1024])
+def test_ragged_input_dims(mck, dev, in_dim):
+    plan = mck.Plan(1024, 2, "rbf", 1.0, 5)
+    x = wl.mnist_like(17, in_dim, seed=in_dim)
+    phi = mck.features(plan, torch.from_numpy(x).to(dev)).cpu().numpy()
+    ref = ff.features(x.astype(np.float64), _oracle_tables(plan))
+    assert _max_err(phi, ref) <= TOL
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 8, 9, 31, 33])
+def test_ragged_batches(mck, dev, n):
+    for d in (32, 128, 1024):
+        plan = mck.Plan(d, 3, "rbf", 1.0, 11)
+        x = wl.gaussian(n, d, seed=n) * np.float32(0.3)
+        phi = mck.features(plan, torch.from_numpy(x).to(dev)).cpu().numpy()
+        ref = ff.features(x.astype(np.float64), _oracle_tables(plan))
+        assert _max_err(phi, ref) <= TOL
+
+
+def test_strided_and_misaligned_rows(mck, dev):
+    plan = mck.Plan(1024, 2, "rbf", 1.0, 13)
+    base = wl.mnist_like(10, 900, seed=3)
+    t = torch.from_numpy(base).to(dev)
+    ref_tab = _oracle_tables(plan)
+    # rows with leading dimension 900 > in_dim 784
+    phi = mck.features(plan, t[:, :784]).cpu().numpy()
+    assert _max_err(phi, ff.features(base[:, :784].astype(np.float64), ref_tab)) <= TOL
+    # rows starting one float past a 16-byte boundary (scalar load path)
+    phi = mck.features(plan, t[:, 1:785]).cpu().numpy()
+    assert _max_err(phi, ff.features(base[:, 1:785].astype(np.float64), ref_tab)) <= TOL
+
+
+def test_empty_batch(mck, dev):
+    plan = mck.Plan(1024, 2, "rbf", 1.0, 1)
+    out = mck.features(plan, torch.empty((0, 784), device=dev))
+    assert out.shape == (0, 4096)
+
+
+@pytest.mark.parametrize("d", [8, 256, 1024, 4096])
+def test_overridden_calibration_and_gaussian(mck, dev, d):
+    plan = mck.Plan(d, 2, "rbf", 1.0, 17)
+    T = _oracle_tables(plan)
+    g = np.random.default_rng(d)
+    Cs = (T["Cs"] * (1 + 0.1 * g.standard_normal(T["Cs"].shape))).astype(np.float32)
+    G = (T["G"] + 0.1 * g.standard_normal(T["G"].shape)).astype(np.float32)
+    x = wl.mnist_like(5, min(d, 784), seed=2)
+    phi = mck.features(plan, torch.from_numpy(x).to(dev), torch.from_numpy(Cs).to(dev),
+                       torch.from_numpy(G).to(dev)).cpu().numpy()
+    T2 = dict(T, Cs=Cs.astype(np.float64), G=G.astype(np.float64))
+    assert _max_err(phi, ff.features(x.astype(np.float64), T2)) <= TOL
+
+
+@pytest.mark.parametrize("d", [64, 256, 512])
+def test_matern(mck, dev, d):
+    plan = mck.Plan(d, 2, "matern", 1.0, 1398239763, matern_t=40)
+    x = wl.mnist_like(6, min(d, 784), seed=4)
+    phi = mck.features(plan, torch.from_numpy(x).to(dev)).cpu().numpy()
+    ref = ff.features(x.astype(np.float64), _oracle_tables(plan))
+    assert _max_err(phi, ref) <= TOL
+
+
+def test_deterministic(mck, dev):
+    plan = mck.Plan(1024, 4, "rbf", 1.0, 42)
+    x = torch.from_numpy(wl.mnist_like(100, 784, seed=1)).to(dev)
+    a = mck.features(plan, x)
+    b = mck.features(plan, x)
+    assert torch.equal(a, b)
+
+
+def _sampled_rows_check(mck, dev, N, E, sigma, kernel="rbf"):
+    d = 1024
+    plan = mck.Plan(d, E, kernel, sigma, 42)
+    x = wl.mnist_like(N, 784, seed=42)
+    phi = mck.features(plan, torch.from_numpy(x).to(dev))
+    rows = np.unique(np.concatenate([[0, 1, 7, 8, N // 2, N - 2, N - 1],
+                                     np.random.default_rng(0).integers(0, N, 25)]))
+    got = phi[torch.from_numpy(rows).to(dev)].cpu().numpy()
+    del phi
+    ref = ff.features(x[rows].astype(np.float64), _oracle_tables(plan))
+    assert _max_err(got, ref) <= TOL
+
+
+def test_config1_full_size_sampled(mck, dev):
+    # N=60000, E=8, sigma=3, RBF: 3.9 GB of features, checked on sampled rows.
+    _sampled_rows_check(mck, dev, 60000, 8, 3.0)
+
+
+def test_headline_full_size_sampled(mck, dev):
+    # N=60000, d=1024, E=16, sigma=3: 7.9 GB of features, checked on sampled rows.
+    _sampled_rows_check(mck, dev, 60000, 16, 3.0)
+    torch.cuda.empty_cache()
