@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--no-extras", action="store_true", help="skip train_step/fused_logits/e2e/cpu legs")
+    p.add_argument("--batch", type=int, default=N,
+                   help="rows per GPU (default 60000; smaller values are for profiling captures)")
     return p.parse_args()
 
 
@@ -203,10 +205,11 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     build.build()
 
+    nb = args.batch
     plan = mck.Plan(D, E, "rbf", SIGMA, SEED)
-    x_host = wl.mnist_like(N, IN_DIM, seed=SEED + rank)
+    x_host = wl.mnist_like(nb, IN_DIM, seed=SEED + rank)
     x = torch.from_numpy(x_host).to(dev)
-    phi = torch.empty((N, F), device=dev)
+    phi = torch.empty((nb, F), device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def barrier():
@@ -235,22 +238,23 @@ def main():
     ms = mdist.max_over_ranks(ms_local, device=dev)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     avg_launch_s = statistics.mean(launch_ms) / 1e3
-    value = world * N * F * args.steps / (ms / 1e3)
+    value = world * nb * F * args.steps / (ms / 1e3)
 
     bytes_per_row = IN_DIM * 4 + F * 4
     peak, peak_kind = measured_peaks()
-    achieved = N * bytes_per_row / avg_launch_s / 1e9
+    achieved = nb * bytes_per_row / avg_launch_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
-                "kernel": "k_feat_warp<10,0>", "bytes_per_launch": N * bytes_per_row,
+                "kernel": "k_feat_warp<10,0>", "bytes_per_launch": nb * bytes_per_row,
                 "traffic": ncu_traffic("k_feat_warp<10,0>")}
 
     line = {"metric": METRIC, "value": value, "unit": "features/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (MNIST-shaped stand-in, seeded)",
-            "config": dict(WORKLOAD, parallelism=f"dp{world} (samples sharded, no collective)"),
-            "hbm_gbs": world * N * bytes_per_row * args.steps / (ms / 1e3) / 1e9,
+            "config": dict(WORKLOAD, batch_per_gpu=nb,
+                           parallelism=f"dp{world} (samples sharded, no collective)"),
+            "hbm_gbs": world * nb * bytes_per_row * args.steps / (ms / 1e3) / 1e9,
             "roofline": roofline, "clocks": clk.summary(), "gpu_launches": args.steps,
             "launch_ms": {"mean": statistics.mean(launch_ms), "min": min(launch_ms),
                           "max": max(launch_ms)}}

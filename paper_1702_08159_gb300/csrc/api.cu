@@ -128,7 +128,7 @@ mck_status_t check_x(const mck_plan_s* p, const float* x, int64_t n, int64_t in_
   if (n < 0) return fail(MCK_EINVAL, "n < 0");
   if (in_dim < 1 || in_dim > p->d) return fail(MCK_EINVAL, "in_dim must be in [1, d]");
   if (ldx < in_dim) return fail(MCK_EINVAL, "ldx < in_dim");
-  if (n == 0) return x ? MCK_OK : fail(MCK_EINVAL, "x is NULL");
+  if (n == 0) return MCK_OK;  // nothing is read; empty tensors may have no storage
   return check_array(x, 4 * ((n - 1) * ldx + in_dim), p->device, "x");
 }
 
@@ -325,8 +325,8 @@ mck_status_t mck_fwht(float* x, int64_t n, int64_t d, int32_t prec, mck_stream_t
   if (!is_pow2(d)) return fail(MCK_EINVAL, "d must be a power of two");
   if (d > ((int64_t)1 << MCK_MAX_LOG2_D_FWHT)) return fail(MCK_EUNSUPPORTED, "d must be <= 2^20");
   if (n < 0) return fail(MCK_EINVAL, "n < 0");
+  if (n == 0 || d == 1) return MCK_OK;  // nothing to transform
   if (!x) return fail(MCK_EINVAL, "x is NULL");
-  if (n == 0 || d == 1) return MCK_OK;
   if (d >= 4 && (uintptr_t)x % 16) return fail(MCK_EINVAL, "x must be 16-byte aligned");
   int device = 0;
   cudaError_t err = cudaGetDevice(&device);
@@ -382,7 +382,12 @@ mck_status_t mck_features_backward(mck_plan_t p, const float* x, int64_t n, int6
   const int64_t F = 2 * p->E * p->d, tb = 4 * p->E * p->d;
   MCK_TRY(check_array(dCs, tb, p->device, "dCs", true));
   MCK_TRY(check_array(dG, tb, p->device, "dG", true));
-  if (n == 0) return MCK_OK;
+  if (n == 0) {  // sums over an empty batch are zero
+    cudaError_t err = cudaSuccess;
+    if (dCs) err = cudaMemsetAsync(dCs, 0, tb, (cudaStream_t)stream);
+    if (dG && err == cudaSuccess) err = cudaMemsetAsync(dG, 0, tb, (cudaStream_t)stream);
+    return launched(err, "mck_features_backward");
+  }
   MCK_TRY(check_array(dphi, 4 * n * F, p->device, "dphi"));
   if ((uintptr_t)dphi % 16) return fail(MCK_EINVAL, "dphi must be 16-byte aligned");
   MCK_TRY(check_array(dx, 4 * ((n - 1) * ldx + in_dim), p->device, "dx", true));

@@ -75,6 +75,7 @@ def test_calls_reject_null_plan_and_arguments(lib):
     assert lib.mck_fwht(v(16), 1, 1 << 21, 0, None) == -5    # beyond 2^20
     assert lib.mck_fwht(v(16), 1, 8, 7, None) == -5          # unknown precision
     assert lib.mck_fwht(None, 1, 8, 0, None) == -1
+    assert lib.mck_fwht(None, 0, 8, 0, None) == 0            # empty: no storage needed
     assert lib.mck_fwht(v(16), -1, 8, 0, None) == -1
     assert lib.mck_fwht(v(16), 0, 8, 0, None) == 0           # empty batch: no-op
     assert lib.mck_softmax_xent(v(16), v(16), -1, 10, None, None, None) == -1

@@ -44,7 +44,10 @@ def test_all_sizes(mck, dev, L):
     n = 9 if L <= 12 else 3
     plan = mck.Plan(d, E, "rbf", 2.0, 1000 + L)
     in_dim = max(1, d - d // 4)
-    x = wl.gaussian(n, in_dim, seed=L) * np.float32(0.5)
+    # ||x|| ~ 6 sigma at every d, as for the MNIST-shaped rows (phases |z| up to ~30).
+    # Much larger phases cannot meet 1e-5 in any float32 path: the spacing of
+    # float32 numbers near |z| = 128 is already 1.5e-5.
+    x = (wl.gaussian(n, in_dim, seed=L) * np.float32(6 * 2.0 / np.sqrt(in_dim))).astype(np.float32)
     phi = mck.features(plan, torch.from_numpy(x).to(dev)).cpu().numpy()
     ref = ff.features(x.astype(np.float64), _oracle_tables(plan))
     assert _max_err(phi, ref) <= TOL
@@ -63,7 +66,7 @@ def test_ragged_input_dims(mck, dev, in_dim):
 def test_ragged_batches(mck, dev, n):
     for d in (32, 128, 1024):
         plan = mck.Plan(d, 3, "rbf", 1.0, 11)
-        x = wl.gaussian(n, d, seed=n) * np.float32(0.3)
+        x = (wl.gaussian(n, d, seed=n) * np.float32(6 / np.sqrt(d))).astype(np.float32)
         phi = mck.features(plan, torch.from_numpy(x).to(dev)).cpu().numpy()
         ref = ff.features(x.astype(np.float64), _oracle_tables(plan))
         assert _max_err(phi, ref) <= TOL

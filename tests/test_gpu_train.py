@@ -146,3 +146,14 @@ def test_backward_deterministic(mck, dev):
     b = mck.features_backward(plan, x, dphi)
     for u, v in zip(a, b):
         assert torch.equal(u, v)
+
+
+def test_empty_batch_gradients_are_zero(mck, dev):
+    plan = mck.Plan(256, 2, "rbf", 1.0, 4)
+    x = torch.empty((0, 200), device=dev)
+    dx, dc, dg = mck.features_backward(plan, x, torch.empty((0, plan.num_features), device=dev))
+    assert dx.shape == (0, 200) and torch.all(dc == 0) and torch.all(dg == 0)
+    W = torch.ones((3, plan.num_features), device=dev)
+    g = mck.fused_logits_backward(plan, x, W, torch.empty((0, 3), device=dev))
+    assert torch.all(g["dW"] == 0) and torch.all(g["db"] == 0) and torch.all(g["dG"] == 0)
+    assert mck.fused_logits(plan, x, W).shape == (0, 3)
