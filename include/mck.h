@@ -149,6 +149,35 @@ mck_status_t mck_fused_logits(mck_plan_t plan, const float* x, int64_t n, int64_
                               const float* b, int32_t num_classes, float* logits,
                               mck_stream_t stream);
 
+/* Capacity, in floats, of the fixed scratch used by mck_fused_logits_noalloc. */
+#define MCK_NOALLOC_MAX_PARTIALS (1 << 22) /* 4,194,304 floats = 16 MiB per device */
+
+/* mck_fused_logits without any memory allocation. (The paper has no
+ * counterpart: this is a library convenience.) Same arguments and results as
+ * mck_fused_logits. It is for callers that must not allocate device memory
+ * while they run -- for example a serving loop that fixes its memory budget
+ * at start-up and must not pay allocation latency or risk an out-of-memory
+ * failure mid-request, or code that manages all device memory through its
+ * own pool and forbids other allocations.
+ *
+ * Instead of stream-ordered scratch, the n x E x num_classes partial logits
+ * go to an array of MCK_NOALLOC_MAX_PARTIALS floats (16 MiB) compiled into
+ * the library; each GPU on which the library is used holds its own copy
+ * until the process exits. Requests with n * E * num_classes above that size
+ * return MCK_EINVAL before any work is queued (split the batch instead).
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture. The call performs no cudaMalloc or cudaFree and calls no
+ * allocating library routine. All calls share the one array per device and
+ * every call fully overwrites the part it uses, so nothing carries over from
+ * a previous call; but calls whose work overlaps on the GPU (different
+ * streams, or different threads) race on the array and must be serialised by
+ * the caller. */
+mck_status_t mck_fused_logits_noalloc(mck_plan_t plan, const float* x, int64_t n, int64_t in_dim,
+                                      int64_t ldx, const float* Cs, const float* G,
+                                      const float* W, const float* b, int32_t num_classes,
+                                      float* logits, mck_stream_t stream);
+
 /* Gradients of sum(logits * dlogits) for mck_fused_logits: dx, dCs, dG, dW
  * (num_classes x 2Ed) and db (num_classes); any output may be NULL. */
 mck_status_t mck_fused_logits_backward(mck_plan_t plan, const float* x, int64_t n,

@@ -487,3 +487,70 @@ mck_status_t mck_softmax_xent(const float* logits, const int32_t* labels, int64_
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free fused logits.
+//
+// mck_fused_logits takes n x E x C floats of stream-ordered scratch for the
+// per-(sample, expansion) partial logits. This variant keeps that scratch in
+// a fixed array compiled into the library instead, so a call performs no
+// allocation at all. The array lives in device memory of every GPU on which
+// the library's code is loaded, for the life of the process.
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __align__(256) float g_noalloc_partials[MCK_NOALLOC_MAX_PARTIALS];
+
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[64] = {};
+
+// Device address of the fixed scratch on `device` (which must be current).
+// In host code the array's name is only a host-side handle, so the address
+// is looked up once per device and cached.
+mck_status_t noalloc_scratch(int device, float** out) {
+  if (device < 0 || device >= 64) return fail(MCK_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    const cudaError_t err = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (err != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_fail(err, "cudaGetSymbolAddress(fixed logits scratch)");
+    }
+    g_noalloc_ptr[device] = static_cast<float*>(p);
+  }
+  *out = g_noalloc_ptr[device];
+  return MCK_OK;
+}
+
+}  // namespace
+
+extern "C" mck_status_t mck_fused_logits_noalloc(mck_plan_t p, const float* x, int64_t n,
+                                                 int64_t in_dim, int64_t ldx, const float* Cs,
+                                                 const float* G, const float* W, const float* b,
+                                                 int32_t C, float* logits, mck_stream_t stream) {
+  MCK_TRY(check_plan(p));
+  if (C < 1 || C > MCK_MAX_CLASSES) return fail(MCK_EINVAL, "num_classes must be in [1, 16]");
+  if (n > 0 && n * (int64_t)p->E * C > (int64_t)MCK_NOALLOC_MAX_PARTIALS)
+    return fail(MCK_EINVAL, "n * E * num_classes = " + std::to_string(n * (int64_t)p->E * C) +
+                                " partial logits exceed the fixed scratch of " +
+                                std::to_string((int64_t)MCK_NOALLOC_MAX_PARTIALS) +
+                                " (split the batch)");
+  DeviceScope scope(p->device);
+  if (!scope.ok) return fail(MCK_ECUDA, "cannot select the plan's device");
+  MCK_TRY(check_x(p, x, n, in_dim, ldx));
+  MCK_TRY(check_tables(p, Cs, G));
+  const int64_t F = 2 * p->E * p->d;
+  MCK_TRY(check_array(W, 4 * C * F, p->device, "W"));
+  if (p->d >= 4 && (uintptr_t)W % 16) return fail(MCK_EINVAL, "W must be 16-byte aligned");
+  MCK_TRY(check_array(b, 4 * C, p->device, "b", true));
+  float* scratch = nullptr;
+  MCK_TRY(noalloc_scratch(p->device, &scratch));
+  if (n == 0) return MCK_OK;
+  MCK_TRY(check_array(logits, 4 * n * C, p->device, "logits"));
+  // Every partial read by the reduction is written first by the feature
+  // kernel of this call, so the array needs no clearing between calls.
+  return launched(launch_logits(feature_args(p, x, n, in_dim, ldx, Cs, G), W, b, C, scratch,
+                                logits, (cudaStream_t)stream),
+                  "mck_fused_logits_noalloc");
+}

@@ -1,0 +1,70 @@
+"""The allocation-free fused-logits entry point, called through the C ABI.
+
+mck_fused_logits_noalloc serves callers that must not allocate device memory
+while they run (for example a serving loop with a memory budget fixed at
+start-up): it keeps its partial logits in a fixed 16 MiB array inside the
+library instead of stream-ordered scratch. These tests check that two calls
+in a row match the allocating entry point, and that oversized requests are
+refused before any work is queued. This file is collected last on purpose.
+"""
+
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4  # the logits tolerance of the other fused-logits tests
+
+
+def _call(lib, fn, plan, x, W, b, out):
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    n, in_dim = x.shape
+    bp = ctypes.c_void_p(b.data_ptr()) if b is not None else ctypes.c_void_p(0)
+    return getattr(lib, fn)(plan.handle, ctypes.c_void_p(x.data_ptr()), n, in_dim, in_dim,
+                            None, None, ctypes.c_void_p(W.data_ptr()), bp, W.shape[0],
+                            ctypes.c_void_p(out.data_ptr()), s)
+
+
+def test_noalloc_matches_allocating_entry_point_twice(mck, dev):
+    from paper_1702_08159_gb300 import _lib
+
+    lib = _lib.load()
+    plan = mck.Plan(1024, 4, "rbf", 1.0, 42)
+    C = 10
+    W = torch.from_numpy(wl.logit_weights(C, plan.num_features, seed=3, std=0.05)[0]).to(dev)
+    b = torch.linspace(-1, 1, C, device=dev)
+    for call, (n, seed) in enumerate([(1000, 1), (333, 2)]):
+        x = torch.from_numpy(wl.mnist_like(n, 784, seed=seed)).to(dev)
+        ref = torch.empty((n, C), device=dev)
+        got = torch.full((n, C), float("nan"), device=dev)
+        assert _call(lib, "mck_fused_logits", plan, x, W, b, ref) == 0
+        assert _call(lib, "mck_fused_logits_noalloc", plan, x, W, b, got) == 0, \
+            lib.mck_last_error()
+        torch.cuda.synchronize()
+        err = (got - ref).abs().max().item()
+        assert err <= TOL, (call, err)
+
+
+def test_noalloc_refuses_oversized_batch(mck, dev):
+    from paper_1702_08159_gb300 import _lib
+
+    lib = _lib.load()
+    plan = mck.Plan(64, 8, "rbf", 1.0, 1)
+    C = 16
+    limit = 1 << 22
+    n = limit // (8 * C) + 1      # one row past the fixed scratch
+    x = torch.zeros((2, 64), device=dev)
+    W = torch.zeros((C, plan.num_features), device=dev)
+    out = torch.zeros((2, C), device=dev)
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = lib.mck_fused_logits_noalloc(plan.handle, ctypes.c_void_p(x.data_ptr()), n, 64, 64,
+                                      None, None, ctypes.c_void_p(W.data_ptr()), None, C,
+                                      ctypes.c_void_p(out.data_ptr()), s)
+    assert st == -1
+    assert b"fixed scratch" in lib.mck_last_error()
+    assert np.all(out.cpu().numpy() == 0)  # nothing ran
