@@ -143,6 +143,9 @@ FeatureArgs feature_args(const mck_plan_s* p, const float* x, int64_t n, int64_t
   a.perm = p->perm;
   a.G = G ? G : p->G;
   a.Cs = Cs ? Cs : p->Cs;
+  a.permB = p->permB;
+  a.GB = G ? nullptr : p->GB;  // an overriding G is read in natural order
+  a.maskA = p->maskA;
   a.E = p->E;
   a.L = p->L;
   a.num_sms = p->num_sms;
@@ -254,6 +257,12 @@ mck_status_t mck_plan_ex(mck_plan_t* out, int64_t d, int32_t E, int32_t kernel, 
             cudaMalloc(&p->perm, sizeof(uint32_t) * n) == cudaSuccess &&
             cudaMalloc(&p->G, sizeof(float) * n) == cudaSuccess &&
             cudaMalloc(&p->Cs, sizeof(float) * n) == cudaSuccess;
+  if (ok && p->L >= 5 && p->L <= 10) {
+    const size_t T = (size_t)1 << (p->L - 5);
+    ok = cudaMalloc(&p->permB, sizeof(uint32_t) * n) == cudaSuccess &&
+         cudaMalloc(&p->GB, sizeof(float) * n) == cudaSuccess &&
+         cudaMalloc(&p->maskA, sizeof(uint32_t) * T * E) == cudaSuccess;
+  }
   if (!ok) {
     cudaGetLastError();
     mck_plan_destroy(p);
@@ -288,6 +297,9 @@ void mck_plan_destroy(mck_plan_t p) {
     cudaFree(p->perm);
     cudaFree(p->G);
     cudaFree(p->Cs);
+    cudaFree(p->permB);
+    cudaFree(p->GB);
+    cudaFree(p->maskA);
     cudaGetLastError();
   }
   delete p;

@@ -136,11 +136,15 @@ __device__ __forceinline__ void epilogue_A(const Launch& P, int64_t n, int e, bo
 // ---------------------------------------------------------------------------
 // Warp kernel, 5 <= L <= 10.
 // ---------------------------------------------------------------------------
+// Work item = (tile of SPI samples, expansion). Small tiles keep a warp's
+// input rows resident in L1 while it walks the expansions of its tile; the
+// cost is one table load per item, which the lane-ordered tables keep to a
+// few coalesced loads.
 template <int L>
 struct WarpShape {
   static constexpr int T = Lay<L>::T;
   static constexpr int VPW = 32 / T;                 // samples per warp step
-  static constexpr int R = VPW >= 8 ? 1 : 8 / VPW;   // steps per item
+  static constexpr int R = VPW >= 4 ? 1 : 4 / VPW;   // steps per item
   static constexpr int SPI = VPW * R;                // samples per item
 };
 
@@ -182,13 +186,31 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_feat_warp(const Launch P) {
     if (e != cur_e) {
       cur_e = e;
       const int64_t off = (int64_t)e * d;
-      bmask = load_bmask_A<L>(P.a.B_bits + (int64_t)e * (d / 32), lam);
+      // Lane-ordered tables: entry (m, lam, q) holds element kB(lam, 4m+q).
+      bmask = __ldg(P.a.maskA + (int64_t)e * Y::T + lam);
+      const uint32_t slot = buf_addr + 4u * (uint32_t)(g * Y::SLOT);
+      const uint4* pb = reinterpret_cast<const uint4*>(P.a.permB + off) + lam;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int k = Y::kB(lam, j);
-        gt[j] = __ldg(P.a.G + off + k);
-        const uint32_t src = __ldg(P.a.perm + off + k);
-        paddr[j] = buf_addr + 4u * (uint32_t)spos<L>(g, (int)src);
+      for (int m = 0; m < 8; ++m) {
+        const uint4 v = __ldg(pb + m * Y::T);
+        paddr[4 * m] = slot + v.x;
+        paddr[4 * m + 1] = slot + v.y;
+        paddr[4 * m + 2] = slot + v.z;
+        paddr[4 * m + 3] = slot + v.w;
+      }
+      if (P.a.GB) {
+        const float4* gb = reinterpret_cast<const float4*>(P.a.GB + off) + lam;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const float4 v = __ldg(gb + m * Y::T);
+          gt[4 * m] = v.x;
+          gt[4 * m + 1] = v.y;
+          gt[4 * m + 2] = v.z;
+          gt[4 * m + 3] = v.w;
+        }
+      } else {  // caller-supplied G, natural order
+#pragma unroll
+        for (int j = 0; j < 32; ++j) gt[j] = __ldg(P.a.G + off + Y::kB(lam, j));
       }
 #pragma unroll
       for (int m = 0; m < 8; ++m) {
@@ -204,6 +226,21 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_feat_warp(const Launch P) {
       const bool valid = n < P.a.n;
       float w[32];
       load_x_A<L>(P, n, valid, lam, w);
+      // Ask L1 for the next sample's row now; it is needed one sample later.
+      {
+        int64_t nn;
+        bool more = true;
+        if (r + 1 < WS::R) {
+          nn = n + WS::VPW;
+        } else {
+          const int64_t it2 = it + 1;
+          more = it2 < it1;
+          const int64_t tile2 = (MODE == MODE_FEATURES) ? it2 / E : it2 % tiles;
+          nn = tile2 * WS::SPI + g;
+        }
+        if (more && nn < P.a.n && (int64_t)lam * 32 < P.a.in_dim)
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(P.a.x + nn * P.a.ldx + lam * 32));
+      }
       apply_signs(w, bmask);
       // u = H B x-hat
       hreg<Y::maskA()>(w);

@@ -23,6 +23,12 @@ struct mck_plan_s {
   float* G = nullptr;          // E x d
   float* Cs = nullptr;         // E x d
   int64_t words = 0;           // ceil(d / 32)
+  // Lane-ordered copies for the warp kernels (32 <= d <= 1024), built at plan
+  // time so a warp loads an expansion's tables with coalesced 128-bit loads:
+  // entry (e, m, lam, q) describes element k = kB(lam, 4m+q) of layout B.
+  uint32_t* permB = nullptr;   // E x d: byte offset 4*pad(pi_e(k)) inside a vector slot
+  float* GB = nullptr;         // E x d: G_e[k]
+  uint32_t* maskA = nullptr;   // E x T: bit j set where B_e[kA(lam, j)] = -1
 };
 
 namespace mck {
@@ -47,6 +53,9 @@ struct FeatureArgs {
   const uint32_t* perm;
   const float* G;
   const float* Cs;
+  const uint32_t* permB;  // lane-ordered tables (warp kernels); null when absent
+  const float* GB;        // null when G is overridden by the caller
+  const uint32_t* maskA;
   int32_t E;
   int L;
   int num_sms;

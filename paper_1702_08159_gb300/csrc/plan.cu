@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "common.cuh"
 #include "internal.h"
 #include "philox.cuh"
 
@@ -218,7 +219,41 @@ __global__ void k_plan_perm(uint32_t* __restrict__ perm, int64_t d, uint32_t k0,
   for (int64_t i = threadIdx.x; i < d; i += blockDim.x) perm[(int64_t)e * d + i] = Ls[i];
 }
 
+// Lane-ordered copies of Pi, G and B for the warp kernels (see internal.h):
+// entry t = (e, m, lam, q) of an expansion's d entries describes element
+// k = kB(lam, 4m + q); the mask word (e, lam) has bit j for element kA(lam, j).
+template <int L>
+__global__ void k_plan_lane_tables(const uint32_t* __restrict__ perm, const float* __restrict__ G,
+                                   const uint32_t* __restrict__ bits, uint32_t* __restrict__ permB,
+                                   float* __restrict__ GB, uint32_t* __restrict__ maskA, int32_t E) {
+  using Y = Lay<L>;
+  constexpr int d = Y::d, T = Y::T;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)E * d) return;
+  const int64_t e = t / d;
+  const int r = (int)(t % d);
+  const int q = r & 3, lam = (r >> 2) % T, m = (r >> 2) / T;
+  const int k = Y::kB(lam, 4 * m + q);
+  permB[t] = 4u * (uint32_t)pad((int)perm[e * d + k]);
+  GB[t] = G[e * d + k];
+  if (m == 0 && q == 0) {
+    uint32_t mask = 0;
+    for (int j = 0; j < 32; ++j) {
+      const int kk = Y::kA(lam, j);
+      mask |= ((bits[e * (d / 32) + (kk >> 5)] >> (kk & 31)) & 1u) << j;
+    }
+    maskA[e * T + lam] = mask;
+  }
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <int L>
+void launch_lane_tables(mck_plan_s* p, cudaStream_t s) {
+  k_plan_lane_tables<L><<<blocks_for(p->d * p->E, 256), 256, 0, s>>>(p->perm, p->G, p->B_bits,
+                                                                     p->permB, p->GB, p->maskA,
+                                                                     p->E);
+}
 
 }  // namespace
 
@@ -251,6 +286,18 @@ mck_status_t build_tables(mck_plan_s* p, cudaStream_t s) {
                              (int)perm_smem);
   if (err == cudaSuccess) {
     k_plan_perm<<<(unsigned)E, 1024, perm_smem, s>>>(p->perm, d, k0, k1);
+    err = cudaGetLastError();
+  }
+  if (err == cudaSuccess && p->permB) {
+    switch (p->L) {
+      case 5: launch_lane_tables<5>(p, s); break;
+      case 6: launch_lane_tables<6>(p, s); break;
+      case 7: launch_lane_tables<7>(p, s); break;
+      case 8: launch_lane_tables<8>(p, s); break;
+      case 9: launch_lane_tables<9>(p, s); break;
+      case 10: launch_lane_tables<10>(p, s); break;
+      default: break;
+    }
     err = cudaGetLastError();
   }
   cudaFreeAsync(G64, s);
