@@ -19,6 +19,7 @@ Reported:
              + torch cross-entropy + adjoint from dphi), both at equal accuracy
   fused_logits softmax-ready logits of the same 60000-row batch without
              writing features
+  fwht_sweep   config 2: the standalone transform over 1 GiB batches, d = 2^10..2^20
   cpu_baseline the FP64 oracle on a bounded sample of the same workload
 
 --impl reference times the oracle itself (CPU) on the same workload, as the
@@ -51,7 +52,7 @@ CPU_SAMPLE_ROWS = 1536
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--no-extras", action="store_true", help="skip train_step/fused_logits/e2e/cpu legs")
@@ -91,54 +92,84 @@ def ncu_traffic(kernel):
 
 
 class ClockSampler:
-    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+    """nvidia-smi samples (SM clock, throttle reasons) taken during the timed region.
+
+    Samples are read on a thread with host timestamps; ``mark_start`` and
+    ``mark_end`` bracket the timed region and ``summary`` keeps the samples
+    inside it (or the nearest one when the region is shorter than the
+    sampling interval).
+    """
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.samples = []
+        self.t0 = self.t1 = None
 
     def __enter__(self):
+        import threading
+
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "10"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return self
+
+        def reader():
+            for line in self.proc.stdout:
+                self.samples.append((time.time(), line))
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+        deadline = time.time() + 5.0
+        while not self.samples and time.time() < deadline:
+            time.sleep(0.01)
         return self
 
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+        time.sleep(0.03)  # let the sample covering the end arrive
+
     def __exit__(self, *a):
-        self.out = ""
         if self.proc is not None:
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in (self.out or "").strip().splitlines():
-            f = [s.strip() for s in line.split(",")]
+        parsed = []
+        for t, line in self.samples:
+            f = [v.strip() for v in line.split(",")]
             if len(f) < 9:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
+                parsed.append((t, float(f[1]), float(f[2]), f[5:9]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+        if not parsed:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        t0, t1 = self.t0 or parsed[0][0], self.t1 or parsed[-1][0]
+        inside = [p for p in parsed if t0 <= p[0] <= t1]
+        if not inside:
+            inside = [min(parsed, key=lambda p: abs(p[0] - 0.5 * (t0 + t1)))]
+        reasons = sorted({nm for p in inside for nm, v in zip(self.NAMES, p[3])
+                          if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(p[1] for p in inside), "sm_max_mhz": inside[0][2],
+                "reasons": reasons, "samples_in_region": len(inside),
+                "region_ms": 1e3 * (t1 - t0)}
 
 
 def cpu_baseline(rows=CPU_SAMPLE_ROWS):
@@ -226,6 +257,7 @@ def main():
     with ClockSampler(local) as clk:
         t_start = torch.cuda.Event(enable_timing=True)
         t_end = torch.cuda.Event(enable_timing=True)
+        clk.mark_start()
         t_start.record(stream)
         for i in range(args.steps):
             ev[i][0].record(stream)
@@ -233,6 +265,7 @@ def main():
             ev[i][1].record(stream)
         t_end.record(stream)
         torch.cuda.synchronize()
+        clk.mark_end()
     barrier()
     ms_local = t_start.elapsed_time(t_end)
     ms = mdist.max_over_ranks(ms_local, device=dev)
@@ -263,6 +296,7 @@ def main():
         line["e2e"] = e2e_leg(mck, plan, x_host, dev, stream, world)
         line["fused_logits"] = fused_logits_leg(mck, plan, x, dev, stream, args)
         line["train_step"] = train_step_leg(mck, dev, stream, args)
+        line["fwht_sweep"] = fwht_sweep_leg(mck, dev, stream, args)
     del phi
     if rank == 0 and world == 1 and not args.no_extras:
         line["cpu_baseline"] = cpu_baseline()
@@ -329,6 +363,55 @@ def fused_logits_leg(mck, plan, x, dev, stream, args):
     # FP32 FMAs: features' transforms are not counted; the contraction is C*2Ed per row.
     return {"samples_per_s": N / (ms / 1e3), "features_per_s": N * F / (ms / 1e3),
             "ms_per_call": ms, "num_classes": C, "gpu_launches_per_call": 2}
+
+
+def fwht_sweep_leg(mck, dev, stream, args):
+    """Config 2: in-place transform of 1 GiB of N(0,1) float32 at d = 2^10..2^20.
+
+    Per d: the mean CUDA-event time of one launch (input restored between
+    launches), GB/s at 8 bytes per element (read + write once), the fraction
+    of the measured HBM bandwidth, and the max error of sampled rows against
+    the FP64 oracle relative to sqrt(d) * rms(x).
+    """
+    import torch
+
+    import workloads as wl
+    from oracle import fastfood as ff
+
+    total = 1 << 28
+    host = wl.gaussian(1, total, seed=SEED).reshape(-1)
+    x0 = torch.from_numpy(host).to(dev)
+    work = torch.empty_like(x0)
+    peak, _ = measured_peaks()
+    out = []
+    for L in range(10, 21):
+        d = 1 << L
+        n = total // d
+        rows = min(n, max(1, (1 << 22) // d))
+        work.copy_(x0)
+        mck.fwht_(work.view(n, d))
+        torch.cuda.synchronize()
+        got = work[: rows * d].view(rows, d).cpu().numpy().astype(np.float64)
+        xin = host[: rows * d].reshape(rows, d).astype(np.float64)
+        ref = ff.fwht(xin)
+        rel = float(np.abs(got - ref).max() / (np.sqrt(d) * np.sqrt((xin ** 2).mean())))
+        times = []
+        for i in range(args.warmup + max(3, args.steps // 4)):
+            work.copy_(x0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mck.fwht_(work.view(n, d))
+            b.record(stream)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                times.append(a.elapsed_time(b))
+        ms = statistics.mean(times)
+        gbs = 8.0 * total / (ms / 1e3) / 1e9
+        out.append({"d": d, "batch": n, "ms": ms, "gbs": gbs, "frac_of_measured_hbm": gbs / peak,
+                    "passes": 1 if L <= 15 else 2, "max_err_rel_sqrt_d_rms": rel,
+                    "err_rows": rows})
+    del work, x0
+    return {"dtype": "f32", "elements_per_d": total, "sizes": out}
 
 
 def train_step_leg(mck, dev, stream, args):

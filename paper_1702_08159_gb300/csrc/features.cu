@@ -17,7 +17,8 @@
 //              each); a warp processes 32/2^(L-5) samples at once. Work items
 //              are (tile of samples, expansion); a warp loads the expansion's
 //              tables into registers once per item (B as a bit mask, G, Cs and
-//              the gather addresses of Pi) and runs the item's samples.
+//              the gather offsets of Pi, packed two per register) and runs
+//              the item's samples.
 //   L = 11..15 block kernel: one block of 2^(L-5) threads per (sample, e).
 //   L = 1..4   one thread per (sample, e).
 #include <cuda_runtime.h>
@@ -32,7 +33,11 @@ namespace {
 
 constexpr int MODE_FEATURES = 0;
 constexpr int MODE_LOGITS = 1;
-constexpr int kWarps = 4;   // warps per block of the warp kernel
+// One warp per block: with 128 registers a thread, 16 single-warp blocks fit
+// on an SM, the most residency the register file allows while the tables of
+// one expansion stay in registers.
+constexpr int kWarps = 1;
+constexpr int kWarpMinBlocks = 14;  // feature mode; the logits mode keeps its accumulators unspilled
 constexpr int CMAX = MCK_MAX_CLASSES;
 
 struct Launch {
@@ -149,7 +154,7 @@ struct WarpShape {
 };
 
 template <int L, int MODE>
-__global__ void __launch_bounds__(kWarps * 32, 3) k_feat_warp(const Launch P) {
+__global__ void __launch_bounds__(kWarps * 32, MODE == MODE_FEATURES ? kWarpMinBlocks : 12) k_feat_warp(const Launch P) {
   using Y = Lay<L>;
   using WS = WarpShape<L>;
   constexpr int d = Y::d;
@@ -168,7 +173,8 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_feat_warp(const Launch P) {
 
   uint32_t bmask = 0;
   float gt[32], cs[32];
-  uint32_t paddr[32];
+  uint32_t poff[16];  // gather byte offsets inside the slot, two 16-bit values each
+  uint32_t pslot = 0;
   int cur_e = -1;
 
   for (int64_t it = it0; it < it1; ++it) {
@@ -189,14 +195,14 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_feat_warp(const Launch P) {
       // Lane-ordered tables: entry (m, lam, q) holds element kB(lam, 4m+q).
       bmask = __ldg(P.a.maskA + (int64_t)e * Y::T + lam);
       const uint32_t slot = buf_addr + 4u * (uint32_t)(g * Y::SLOT);
+      // Gather offsets are below 2^16 bytes: two per register.
+      pslot = slot;
       const uint4* pb = reinterpret_cast<const uint4*>(P.a.permB + off) + lam;
 #pragma unroll
       for (int m = 0; m < 8; ++m) {
         const uint4 v = __ldg(pb + m * Y::T);
-        paddr[4 * m] = slot + v.x;
-        paddr[4 * m + 1] = slot + v.y;
-        paddr[4 * m + 2] = slot + v.z;
-        paddr[4 * m + 3] = slot + v.w;
+        poff[2 * m] = v.x | (v.y << 16);
+        poff[2 * m + 1] = v.z | (v.w << 16);
       }
       if (P.a.GB) {
         const float4* gb = reinterpret_cast<const float4*>(P.a.GB + off) + lam;
@@ -254,7 +260,8 @@ __global__ void __launch_bounds__(kWarps * 32, 3) k_feat_warp(const Launch P) {
       store_B<L>(buf, g, lam, w);
       __syncwarp();
 #pragma unroll
-      for (int j = 0; j < 32; ++j) w[j] = lds32(paddr[j]);
+      for (int j = 0; j < 32; ++j)
+        w[j] = lds32(pslot + ((j & 1) ? (poff[j >> 1] >> 16) : (poff[j >> 1] & 0xffffu)));
       // h = H G v (G folded into the first butterfly stage)
       hreg_scaled<Y::maskB()>(w, gt);
       if constexpr (L > 5) {
