@@ -64,7 +64,11 @@ typedef enum {
 } mck_status_t;
 
 typedef enum {
-  MCK_FP32 = 0  /* the transform in float32 arithmetic */
+  MCK_FP32 = 0,       /* float32 butterflies */
+  MCK_BF16 = 1,       /* H16 digits as bf16 tensor-core products, FP32 accumulation */
+  MCK_FP16 = 2,       /* the same with fp16 operands */
+  MCK_BF16_SPLIT = 3, /* bf16 with each operand split into hi + lo halves (two products) */
+  MCK_FP16_SPLIT = 4  /* fp16 with the hi + lo split */
 } mck_prec_t;
 
 #define MCK_MAX_LOG2_D 15          /* largest plan dimension: d = 2^15 */
@@ -113,8 +117,13 @@ mck_status_t mck_plan_tables(mck_plan_t plan, uint32_t* B_bits, uint32_t* perm, 
  *   x     device, n x d float32, contiguous, 16-byte aligned when d >= 4
  *   n     number of vectors (>= 0)
  *   d     power of two, 1 <= d <= 2^20
- *   prec  MCK_FP32
- * d <= 2^15 runs one pass over HBM; larger d runs two. */
+ *   prec  MCK_FP32: float32 butterflies, any d; d <= 2^15 runs one pass over
+ *         HBM, larger d two.
+ *         MCK_BF16 / MCK_FP16 / *_SPLIT: the Kronecker factorisation
+ *         H_16 (x) H_16 (x) H_{d/256} on tensor cores (16-bit operands, the
+ *         +-1 factor exact, FP32 accumulation; *_SPLIT rounds each operand
+ *         as hi + lo to recover ~16 more bits); d in {256, 512, 1024} and
+ *         n * d a multiple of 1024 (MCK_EUNSUPPORTED / MCK_EINVAL otherwise). */
 mck_status_t mck_fwht(float* x, int64_t n, int64_t d, int32_t prec, mck_stream_t stream);
 
 /* phi = features of n samples (Eq. etn:mckernel, Eq. etn:mcfeatures).

@@ -140,14 +140,21 @@ def _tables(plan, Cs, G):
     return Cs, G
 
 
-def fwht_(x):
-    """In-place unnormalised Walsh-Hadamard transform of the rows of x (last dim d)."""
+def fwht_(x, prec="fp32"):
+    """In-place unnormalised Walsh-Hadamard transform of the rows of x (last dim d).
+
+    prec: "fp32" (float32 butterflies, any d <= 2^20) or, for d in {256, 512,
+    1024}, the tensor-core Kronecker-H16 forms "bf16", "fp16", "bf16_split",
+    "fp16_split" (16-bit operands, FP32 accumulation; *_split = hi + lo).
+    """
     _f32_cuda(x, "x")
     if not x.is_contiguous():
         raise ValueError("x must be contiguous")
     d = x.size(-1)
     n = x.numel() // d if d else 0
-    check(load().mck_fwht(_ptr(x), n, d, _lib.MCK_FP32, _stream(x.device)), "mck_fwht")
+    p = _lib.PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    with torch.cuda.device(x.device):
+        check(load().mck_fwht(_ptr(x), n, d, p, _stream(x.device)), "mck_fwht")
     return x
 
 

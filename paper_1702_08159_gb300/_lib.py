@@ -19,6 +19,11 @@ MCK_EUNSUPPORTED = -5
 MCK_RBF = 0
 MCK_MATERN = 1
 MCK_FP32 = 0
+MCK_BF16 = 1
+MCK_FP16 = 2
+MCK_BF16_SPLIT = 3
+MCK_FP16_SPLIT = 4
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16_split": 3, "fp16_split": 4}
 
 MAX_LOG2_D = 15
 MAX_LOG2_D_FWHT = 20

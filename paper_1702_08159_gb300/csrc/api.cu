@@ -333,8 +333,12 @@ mck_status_t mck_plan_tables(mck_plan_t p, uint32_t* B_bits, uint32_t* perm, flo
 }
 
 mck_status_t mck_fwht(float* x, int64_t n, int64_t d, int32_t prec, mck_stream_t stream) {
-  if (prec != MCK_FP32) return fail(MCK_EUNSUPPORTED, "only MCK_FP32 is implemented");
+  if (prec < MCK_FP32 || prec > MCK_FP16_SPLIT) return fail(MCK_EUNSUPPORTED, "unknown precision");
   if (!is_pow2(d)) return fail(MCK_EINVAL, "d must be a power of two");
+  if (prec != MCK_FP32 && !fwht_mma_supported(log2i(d)))
+    return fail(MCK_EUNSUPPORTED, "the tensor-core transform supports d = 256, 512, 1024");
+  if (prec != MCK_FP32 && ((n * d) & 1023))
+    return fail(MCK_EINVAL, "the tensor-core transform needs n * d to be a multiple of 1024");
   if (d > ((int64_t)1 << MCK_MAX_LOG2_D_FWHT)) return fail(MCK_EUNSUPPORTED, "d must be <= 2^20");
   if (n < 0) return fail(MCK_EINVAL, "n < 0");
   if (n == 0 || d == 1) return MCK_OK;  // nothing to transform
@@ -344,6 +348,9 @@ mck_status_t mck_fwht(float* x, int64_t n, int64_t d, int32_t prec, mck_stream_t
   cudaError_t err = cudaGetDevice(&device);
   if (err != cudaSuccess) return cuda_fail(err, "cudaGetDevice");
   MCK_TRY(check_array(x, 4 * n * d, device, "x"));
+  if (prec != MCK_FP32)
+    return launched(launch_fwht_mma(x, n, log2i(d), prec, sm_count(device), (cudaStream_t)stream),
+                    "mck_fwht");
   return launched(launch_fwht(x, n, log2i(d), sm_count(device), (cudaStream_t)stream), "mck_fwht");
 }
 

@@ -43,6 +43,10 @@ mck_status_t build_tables(mck_plan_s* p, cudaStream_t s);
 // ---- fwht.cu -------------------------------------------------------------
 cudaError_t launch_fwht(float* x, int64_t n, int L, int num_sms, cudaStream_t s);
 
+// ---- fwht_mma.cu -----------------------------------------------------------
+bool fwht_mma_supported(int L);
+cudaError_t launch_fwht_mma(float* x, int64_t n, int L, int prec, int num_sms, cudaStream_t s);
+
 // ---- features.cu -----------------------------------------------------------
 struct FeatureArgs {
   const float* x;

@@ -74,6 +74,8 @@ def test_calls_reject_null_plan_and_arguments(lib):
     assert lib.mck_fwht(v(16), 1, 3, 0, None) == -1          # d not a power of two
     assert lib.mck_fwht(v(16), 1, 1 << 21, 0, None) == -5    # beyond 2^20
     assert lib.mck_fwht(v(16), 1, 8, 7, None) == -5          # unknown precision
+    assert lib.mck_fwht(v(16), 4, 8, 1, None) == -5          # tensor-core form needs d >= 256
+    assert lib.mck_fwht(v(16), 3, 256, 1, None) == -1        # n * d not a multiple of 1024
     assert lib.mck_fwht(None, 1, 8, 0, None) == -1
     assert lib.mck_fwht(None, 0, 8, 0, None) == 0            # empty: no storage needed
     assert lib.mck_fwht(v(16), -1, 8, 0, None) == -1

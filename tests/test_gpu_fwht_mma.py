@@ -1,0 +1,66 @@
+"""Tensor-core Kronecker-H16 transform (mck_fwht with 16-bit precisions) against the oracle.
+
+Error model, relative to sqrt(d) rms(x) (the size of an output): each 16-bit
+rounding of an operand has relative error <= 2^-p (p = 8 for bf16, 11 for fp16
+with round-to-nearest: half an ulp of a p+1-bit significand); an unsplit
+transform rounds twice (the input and the intermediate after the first digit),
+so errors stay near 2^-p; the hi + lo split leaves 2^-2p per rounding. The
+bounds below allow a factor of 4 to 8 over those sizes, far below the O(1)
+error of any wrong index or sign.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as wl
+from oracle import fastfood as ff
+
+pytestmark = pytest.mark.gpu
+
+BOUND = {"bf16": 2.0 ** -6, "fp16": 2.0 ** -8, "bf16_split": 2.0 ** -14, "fp16_split": 2.0 ** -18}
+
+
+def _rel_err(got, x):
+    d = x.shape[1]
+    return float(np.abs(got.astype(np.float64) - ff.fwht(x.astype(np.float64))).max()
+                 / (np.sqrt(d) * np.sqrt((x.astype(np.float64) ** 2).mean())))
+
+
+@pytest.mark.parametrize("prec", list(BOUND))
+@pytest.mark.parametrize("d", [256, 512, 1024])
+def test_tensor_core_transform_accuracy(mck, dev, d, prec):
+    n = (4096 // d) * 3
+    x = wl.gaussian(n, d, seed=d)
+    t = torch.from_numpy(x).to(dev)
+    mck.fwht_(t, prec)
+    err = _rel_err(t.cpu().numpy(), x)
+    assert err <= BOUND[prec], (d, prec, err)
+
+
+@pytest.mark.parametrize("prec", list(BOUND))
+def test_tensor_core_basis_vectors_exact(mck, dev, prec):
+    # H e_i is a row of the Sylvester matrix: +-1 values, exact in every precision.
+    d = 1024
+    t = torch.eye(d, device=dev)
+    mck.fwht_(t, prec)
+    np.testing.assert_array_equal(t.cpu().numpy(), ff.sylvester(d))
+
+
+def test_split_is_more_accurate(mck, dev):
+    x = wl.gaussian(64, 1024, seed=3)
+    errs = {}
+    for prec in ("bf16", "bf16_split", "fp16", "fp16_split"):
+        t = torch.from_numpy(x).to(dev)
+        mck.fwht_(t, prec)
+        errs[prec] = _rel_err(t.cpu().numpy(), x)
+    assert errs["bf16_split"] < errs["bf16"] / 64
+    assert errs["fp16_split"] < errs["fp16"] / 64
+    assert errs["fp16"] < errs["bf16"]
+
+
+def test_tensor_core_rejects_unsupported_shapes(mck, dev):
+    with pytest.raises(mck.MckError, match="UNSUPPORTED"):
+        mck.fwht_(torch.zeros((8, 128), device=dev), "bf16")
+    with pytest.raises(mck.MckError, match="multiple of 1024"):
+        mck.fwht_(torch.zeros((3, 256), device=dev), "bf16")
