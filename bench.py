@@ -20,6 +20,8 @@ Reported:
   fused_logits softmax-ready logits of the same 60000-row batch without
              writing features
   fwht_sweep   config 2: the standalone transform over 1 GiB batches, d = 2^10..2^20
+  uneven_batch config 4: 10000 vectors of mixed d, E and kernel in one persistent
+               graph-launched kernel vs one launch per (d, E, kernel) class
   cpu_baseline the FP64 oracle on a bounded sample of the same workload
 
 --impl reference times the oracle itself (CPU) on the same workload, as the
@@ -297,6 +299,7 @@ def main():
         line["fused_logits"] = fused_logits_leg(mck, plan, x, dev, stream, args)
         line["train_step"] = train_step_leg(mck, dev, stream, args)
         line["fwht_sweep"] = fwht_sweep_leg(mck, dev, stream, args)
+        line["uneven_batch"] = uneven_leg(mck, dev, stream, args)
     del phi
     if rank == 0 and world == 1 and not args.no_extras:
         line["cpu_baseline"] = cpu_baseline()
@@ -438,6 +441,77 @@ def fwht_sweep_leg(mck, dev, stream, args):
                    "max_err_rel_sqrt_d_rms": rel})
     del work, x0
     return {"dtype": "f32", "elements_per_d": total, "sizes": out, "tensor_core_d1024": tc}
+
+
+def uneven_leg(mck, dev, stream, args):
+    """Config 4: 10000 vectors, d = 2^m (m ~ U{6..14}), E ~ U{1..32}, RBF or Matern
+    (t = 40), sigma = 1, N(0,1) entries; plans keyed by (d, kernel) with 32
+    expansions. One graph-launched persistent kernel (autotuned grain) vs one
+    grouped launch per (d, E, kernel) class."""
+    import torch
+
+    import workloads as wl
+    from paper_1702_08159_gb300.tune import tune_grain
+
+    b = wl.uneven_batch(10000, seed=SEED)
+    keys = sorted(set(zip(b["d"].tolist(), b["kernel"].tolist())))
+    plans = [mck.Plan(d, 32, "rbf" if k == 0 else "matern", 1.0, SEED, matern_t=40)
+             for d, k in keys]
+    pidx = np.array([keys.index((d, k)) for d, k in zip(b["d"].tolist(), b["kernel"].tolist())])
+    order = np.lexsort((b["E"], b["kernel"], b["d"]))
+    items, x_len, phi_len = mck.group_layout(plans, pidx, b["E"], b["d"], order)
+    xh = np.zeros(x_len, np.float32)
+    for i, v in enumerate(b["x"]):
+        o = items["x_offset"][i]
+        xh[o: o + len(v)] = v
+    x = torch.from_numpy(xh).to(dev)
+    phi = torch.empty(phi_len, device=dev)
+    feats = int(phi_len)
+    g = mck.Group(plans, items, x_len, phi_len)
+    best, tune_ms = tune_grain(g, x, phi, reps=3)
+    cap = mck.CapturedGroup(g, x, phi)
+
+    def timed(fn, reps):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        e.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(e) / reps
+
+    reps = max(3, args.steps // 5)
+    ms_graph = timed(cap.replay, reps)
+    ms_direct = timed(lambda: g.features(x, phi), reps)
+    # baseline: one grouped launch per (d, E, kernel) class
+    cls = {}
+    for i in range(len(items)):
+        cls.setdefault((int(b["d"][i]), int(b["E"][i]), int(b["kernel"][i])), []).append(i)
+    groups = [mck.Group(plans, items[idx], x_len, phi_len) for idx in cls.values()]
+    phi_b = torch.empty(phi_len, device=dev)
+
+    def per_class():
+        for grp in groups:
+            grp.features(x, phi_b)
+
+    ms_per_class = timed(per_class, reps)
+    torch.cuda.synchronize()
+    same = float((phi - phi_b).abs().max())
+    out = {"vectors": len(items), "features": feats, "plans": len(plans),
+           "classes": len(cls), "tuned_grain": best, "tune_ms": tune_ms,
+           "ms_persistent_graph": ms_graph, "ms_persistent_direct": ms_direct,
+           "ms_per_class_launches": ms_per_class,
+           "features_per_s_persistent": feats / (ms_graph / 1e3),
+           "speedup_vs_per_class": ms_per_class / ms_graph,
+           "gb_per_s_written": 4.0 * feats / (ms_graph / 1e3) / 1e9,
+           "max_abs_diff_vs_per_class": same, "info": g.info()}
+    del phi, phi_b, x, cap, groups, g
+    for pl in plans:
+        pl.close()
+    return out
 
 
 def train_step_leg(mck, dev, stream, args):

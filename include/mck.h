@@ -195,6 +195,51 @@ mck_status_t mck_fused_logits_backward(mck_plan_t plan, const float* x, int64_t 
                                        const float* dlogits, float* dx, float* dCs, float* dG,
                                        float* dW, float* db, mck_stream_t stream);
 
+/* ---- Uneven batches in one persistent launch -------------------------------
+ * A group is a prepared batch of vectors of different padded dimensions,
+ * kernels and expansion counts (each vector uses the first E expansions of
+ * its plan; Sec. "McKernel": expansions are i.i.d. instances of Z-hat). All
+ * its work runs in ONE persistent kernel launch that takes units of work from
+ * an atomic counter. Plans must outlive the group. */
+typedef struct mck_group_s* mck_group_t;
+
+typedef struct {
+  int32_t plan;       /* index into the plans array given to mck_group_create */
+  int32_t E;          /* expansions used: the plan's first E, 1 <= E <= the plan's E */
+  int64_t in_dim;     /* input length, 1 <= in_dim <= the plan's d (zero padded to d) */
+  int64_t x_offset;   /* element offset of the input vector in x */
+  int64_t phi_offset; /* element offset of its 2*E*d features in phi; a multiple of 4 */
+} mck_group_item_t;
+
+/* Build the work list of a group (host work plus a small device upload;
+ * synchronous). plans: host array of num_plans plans on one device with
+ * 32 <= d <= 2^14. items: host array. x_len / phi_len: the element counts of
+ * the x and phi arrays later passed to mck_group_features; every item must
+ * fit inside them. grain: warp steps per warp in one unit of work (0 picks
+ * the default, 2); a tunable, see mck_group_set_grain. Feature layout of an
+ * item: E blocks of [cos (d) | sin (d)] at phi + phi_offset. */
+mck_status_t mck_group_create(mck_group_t* out, const mck_plan_t* plans, int32_t num_plans,
+                              const mck_group_item_t* items, int64_t num_items, int64_t x_len,
+                              int64_t phi_len, int32_t grain);
+
+/* Rebuild the unit list with another grain (1..64); synchronises the device. */
+mck_status_t mck_group_set_grain(mck_group_t group, int32_t grain);
+
+/* Sizes of the work list; any output may be NULL. */
+mck_status_t mck_group_info(mck_group_t group, int64_t* num_units, int64_t* num_warp_steps,
+                            int64_t* num_block_items, int32_t* grain);
+
+/* Features of every item of the group: one memset of the work counter and
+ * one persistent kernel launch on `stream`. Allocates nothing and does not
+ * synchronise, so the call can be captured in a CUDA graph. x (x_len floats)
+ * and phi (phi_len floats, 16-byte aligned) are device arrays. Calls on one
+ * group must not overlap on the GPU (they share the work counter). */
+mck_status_t mck_group_features(mck_group_t group, const float* x, float* phi,
+                                mck_stream_t stream);
+
+/* Release a group (synchronises its device first). NULL is ignored. */
+void mck_group_destroy(mck_group_t group);
+
 /* Mean softmax cross-entropy of logits (n x num_classes) against labels
  * (int32 in [0, num_classes)), the multi-class form of the logistic loss of
  * Eq. etn:loss. loss: device float[1] or NULL; dlogits: device n x

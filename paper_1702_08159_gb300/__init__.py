@@ -249,3 +249,113 @@ def softmax_xent(logits, labels, need_grad=True):
         check(load().mck_softmax_xent(_ptr(logits), _ptr(labels), n, C, _ptr(loss), _ptr(dl),
                                       _stream(logits.device)), "mck_softmax_xent")
     return loss, dl
+
+
+GROUP_ITEM_DTYPE = np.dtype([("plan", "<i4"), ("E", "<i4"), ("in_dim", "<i8"),
+                             ("x_offset", "<i8"), ("phi_offset", "<i8")])
+
+
+class Group:
+    """A prepared uneven batch (mck_group_*): every item's features in one persistent launch.
+
+    plans: list of Plan (32 <= d <= 2^14, one device; kept alive by the group).
+    items: structured array of GROUP_ITEM_DTYPE, or a sequence of
+           (plan_index, E, in_dim, x_offset, phi_offset) tuples.
+    x_len, phi_len: element counts of the x and phi arrays passed to features().
+    """
+
+    def __init__(self, plans, items, x_len, phi_len, grain=0):
+        lib = load()
+        self.plans = list(plans)
+        arr = np.asarray(items, dtype=GROUP_ITEM_DTYPE) if not (
+            isinstance(items, np.ndarray) and items.dtype == GROUP_ITEM_DTYPE) else items
+        arr = np.ascontiguousarray(arr)
+        handles = (ctypes.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        h = ctypes.c_void_p()
+        check(lib.mck_group_create(ctypes.byref(h), handles, len(self.plans),
+                                   arr.ctypes.data if len(arr) else None, len(arr), int(x_len),
+                                   int(phi_len), int(grain)), "mck_group_create")
+        self._h = h
+        self.items = arr
+        self.x_len, self.phi_len = int(x_len), int(phi_len)
+        self.device = self.plans[0].device
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("group is closed")
+        return self._h
+
+    def features(self, x, phi):
+        """Write every item's features into phi (in place); returns phi."""
+        _f32_cuda(x, "x", self.device)
+        _f32_cuda(phi, "phi", self.device)
+        if x.numel() < self.x_len or phi.numel() < self.phi_len:
+            raise ValueError("x or phi smaller than the group's x_len / phi_len")
+        check(load().mck_group_features(self.handle, _ptr(x), _ptr(phi), _stream(x.device)),
+              "mck_group_features")
+        return phi
+
+    def set_grain(self, grain):
+        check(load().mck_group_set_grain(self.handle, int(grain)), "mck_group_set_grain")
+
+    def info(self):
+        u, s, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        g = ctypes.c_int32()
+        check(load().mck_group_info(self.handle, ctypes.byref(u), ctypes.byref(s), ctypes.byref(b),
+                                    ctypes.byref(g)), "mck_group_info")
+        return {"units": u.value, "warp_steps": s.value, "block_items": b.value,
+                "grain": g.value}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().mck_group_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class CapturedGroup:
+    """A Group's launch (counter reset + persistent kernel) captured in a CUDA graph
+    for fixed x and phi; replay() re-runs it with one graph launch."""
+
+    def __init__(self, group, x, phi):
+        self.group, self.x, self.phi = group, x, phi
+        side = torch.cuda.Stream(device=x.device)
+        side.wait_stream(torch.cuda.current_stream(x.device))
+        with torch.cuda.stream(side):
+            group.features(x, phi)  # first call outside capture
+        torch.cuda.current_stream(x.device).wait_stream(side)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            group.features(x, phi)
+
+    def replay(self):
+        self.graph.replay()
+        return self.phi
+
+
+def group_layout(plans, plan_index, E, in_dim, order=None):
+    """Items for a Group with packed x and phi: item i's input occupies
+    x[x_offset : x_offset + in_dim] (slots rounded up to 4 floats) and its
+    features phi[phi_offset : phi_offset + 2 E d]. `order` (default: as given)
+    sets the packing order. Returns (items, x_len, phi_len)."""
+    plan_index = np.asarray(plan_index, dtype=np.int64)
+    E = np.asarray(E, dtype=np.int64)
+    in_dim = np.asarray(in_dim, dtype=np.int64)
+    n = len(plan_index)
+    order = np.arange(n) if order is None else np.asarray(order)
+    d = np.array([plans[p].d for p in plan_index], dtype=np.int64)
+    xs = (in_dim[order] + 3) // 4 * 4
+    fs = 2 * E[order] * d[order]
+    items = np.zeros(n, dtype=GROUP_ITEM_DTYPE)
+    items["plan"][order] = plan_index[order]
+    items["E"][order] = E[order]
+    items["in_dim"][order] = in_dim[order]
+    items["x_offset"][order] = np.concatenate([[0], np.cumsum(xs)[:-1]]) if n else []
+    items["phi_offset"][order] = np.concatenate([[0], np.cumsum(fs)[:-1]]) if n else []
+    return items, int(xs.sum()), int(fs.sum())

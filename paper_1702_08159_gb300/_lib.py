@@ -53,9 +53,23 @@ SIGNATURES = {
     "mck_fused_logits_backward": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _I32, _P, _P, _P,
                                         _P, _P, _P, _P]),
     "mck_softmax_xent": (_ST, [_P, _P, _I64, _I32, _P, _P, _P]),
+    "mck_group_create": (_ST, [ctypes.POINTER(_P), _P, _I32, _P, _I64, _I64, _I64, _I32]),
+    "mck_group_set_grain": (_ST, [_P, _I32]),
+    "mck_group_info": (_ST, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                             ctypes.POINTER(_I32)]),
+    "mck_group_features": (_ST, [_P, _P, _P, _P]),
+    "mck_group_destroy": (None, [_P]),
     "mck_status_string": (ctypes.c_char_p, [_ST]),
     "mck_last_error": (ctypes.c_char_p, []),
 }
+
+
+
+class GroupItem(ctypes.Structure):
+    """mck_group_item_t."""
+    _fields_ = [("plan", _I32), ("E", _I32), ("in_dim", _I64), ("x_offset", _I64),
+                ("phi_offset", _I64)]
+
 
 _lib = None
 

@@ -191,6 +191,10 @@ mck_status_t fail(mck_status_t s, const std::string& msg) {
   return s;
 }
 
+mck_status_t check_device_array(const void* p, int64_t bytes, int device, const char* name) {
+  return check_array(p, bytes, device, name);
+}
+
 mck_status_t cuda_fail(cudaError_t err, const char* where) {
   g_last_error = std::string(where) + ": " + cudaGetErrorName(err) + " (" + cudaGetErrorString(err) + ")";
   return MCK_ECUDA;

@@ -1,0 +1,570 @@
+// Uneven batches in one persistent launch: vectors of different padded
+// dimensions (32 <= d <= 2^14), kernels and expansion counts, each through
+// its own plan (Sec. "McKernel": every expansion is an i.i.d. instance of
+// Z-hat, so a vector may use any prefix of a plan's expansions).
+//
+// mck_group_create turns the items into a work list once:
+//   * d <= 1024: "warp steps" -- up to 32/2^(L-5) vectors that share a plan
+//     and an expansion, processed by one warp exactly like the batched
+//     feature kernel (register layouts A and B, lane-ordered tables);
+//     16 * grain steps form a unit.
+//   * d >= 2048: "block items" -- one (vector, expansion) for a sub-block of
+//     2^(L-5) threads; 512/2^(L-5) items of the same d form a unit, each
+//     sub-block synchronising on its own named barrier.
+// Units are ordered by estimated cost, largest first. The persistent kernel
+// runs one 512-thread block per SM; a block takes the next unit with one
+// atomicAdd on a counter (no thread ever waits for another block) until the
+// list is exhausted. mck_group_features allocates nothing and never blocks
+// the host, so it can be captured in a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace mck {
+namespace {
+
+constexpr int kGThreads = 512;
+constexpr int kGWarps = kGThreads / 32;
+constexpr int kWarpBuf = 1152;      // floats: the largest VPW * SLOT (L = 5)
+constexpr int kSmemFloats = 18432;  // max(16 * kWarpBuf, 512/T sub-blocks * SLOT)
+
+struct GPlan {
+  const uint32_t* permB;
+  const float* GB;
+  const uint32_t* maskA;
+  const float* Cs;
+  const uint32_t* bits;
+  const uint32_t* perm;
+  const float* G;
+  int32_t L;
+  int32_t Emax;
+};
+struct GVec {
+  int64_t x_off;
+  int64_t phi_off;
+  int32_t in_dim;
+  int32_t E;
+};
+struct GStep {
+  int64_t vec_begin;  // into step_vecs
+  int32_t plan;
+  int32_t e;
+  int32_t L;
+  int32_t count;
+};
+struct GItem {
+  int32_t vec;
+  int32_t plan;
+  int32_t e;
+  int32_t L;
+};
+struct GUnit {
+  int64_t begin;
+  int32_t type;  // 0: warp steps, 1: block items
+  int32_t L;     // block items: their common L
+  int32_t count;
+  int32_t pad;
+};
+struct GArgs {
+  const GPlan* plans;
+  const GVec* vecs;
+  const GStep* steps;
+  const int32_t* step_vecs;
+  const GItem* items;
+  const GUnit* units;
+  int64_t num_units;
+  int* counter;
+  const float* x;
+  float* phi;
+  bool vec_x;
+};
+
+__device__ __forceinline__ void named_barrier(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+__device__ __forceinline__ void apply_signs(float (&w)[32], uint32_t mask) {
+#pragma unroll
+  for (int j = 0; j < 32; ++j)
+    w[j] = __int_as_float(__float_as_int(w[j]) ^ ((mask << (31 - j)) & 0x80000000u));
+}
+
+template <int L>
+__device__ __forceinline__ void load_row_A(const float* __restrict__ row, int64_t in_dim,
+                                           bool vec, bool valid, int lam, float (&w)[32]) {
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int k0 = Lay<L>::kA(lam, 4 * m);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+      if (vec) {
+        if (k0 < in_dim) v = __ldg(reinterpret_cast<const float4*>(row + k0));
+      } else {
+        if (k0 + 0 < in_dim) v.x = __ldg(row + k0 + 0);
+        if (k0 + 1 < in_dim) v.y = __ldg(row + k0 + 1);
+        if (k0 + 2 < in_dim) v.z = __ldg(row + k0 + 2);
+        if (k0 + 3 < in_dim) v.w = __ldg(row + k0 + 3);
+      }
+    }
+    w[4 * m] = v.x;
+    w[4 * m + 1] = v.y;
+    w[4 * m + 2] = v.z;
+    w[4 * m + 3] = v.w;
+  }
+}
+
+template <int L>
+__device__ __forceinline__ void store_features_A(float* __restrict__ out, int lam,
+                                                 const float (&h)[32], const float* __restrict__ Cs) {
+  constexpr int d = 1 << L;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int k0 = Lay<L>::kA(lam, 4 * m);
+    const float4 c4 = __ldg(reinterpret_cast<const float4*>(Cs + k0));
+    const float cs[4] = {c4.x, c4.y, c4.z, c4.w};
+    float c[4], s[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cos_sin(cs[q] * h[4 * m + q], c[q], s[q]);
+    __stcs(reinterpret_cast<float4*>(out + k0), make_float4(c[0], c[1], c[2], c[3]));
+    __stcs(reinterpret_cast<float4*>(out + d + k0), make_float4(s[0], s[1], s[2], s[3]));
+  }
+}
+
+// One warp step (5 <= L <= 10): group g of the warp handles vector g of the step.
+template <int L>
+__device__ void warp_step(const GArgs& a, const GStep& st, float* buf, int lane) {
+  using Y = Lay<L>;
+  constexpr int d = Y::d;
+  const int g = lane / Y::T, lam = lane % Y::T;
+  const GPlan pl = a.plans[st.plan];
+  const int64_t off = (int64_t)st.e * d;
+  const uint32_t bmask = __ldg(pl.maskA + (int64_t)st.e * Y::T + lam);
+  const uint32_t slot = smem_addr(buf) + 4u * (uint32_t)(g * Y::SLOT);
+  uint32_t poff[16];
+  float gt[32];
+  const uint4* pb = reinterpret_cast<const uint4*>(pl.permB + off) + lam;
+  const float4* gb = reinterpret_cast<const float4*>(pl.GB + off) + lam;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const uint4 v = __ldg(pb + m * Y::T);
+    poff[2 * m] = v.x | (v.y << 16);
+    poff[2 * m + 1] = v.z | (v.w << 16);
+    const float4 q = __ldg(gb + m * Y::T);
+    gt[4 * m] = q.x;
+    gt[4 * m + 1] = q.y;
+    gt[4 * m + 2] = q.z;
+    gt[4 * m + 3] = q.w;
+  }
+  const bool valid = g < st.count;
+  GVec v{};
+  if (valid) v = a.vecs[a.step_vecs[st.vec_begin + g]];
+  float w[32];
+  load_row_A<L>(a.x + v.x_off, v.in_dim, a.vec_x, valid, lam, w);
+  apply_signs(w, bmask);
+  hreg<Y::maskA()>(w);
+  if constexpr (L > 5) {
+    store_A<L>(buf, g, lam, w);
+    __syncwarp();
+    load_B<L>(buf, g, lam, w);
+  }
+  hreg<Y::maskB()>(w);
+  store_B<L>(buf, g, lam, w);
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 32; ++j)
+    w[j] = lds32(slot + ((j & 1) ? (poff[j >> 1] >> 16) : (poff[j >> 1] & 0xffffu)));
+  hreg_scaled<Y::maskB()>(w, gt);
+  __syncwarp();
+  if constexpr (L > 5) {
+    store_B<L>(buf, g, lam, w);
+    __syncwarp();
+    load_A<L>(buf, g, lam, w);
+  }
+  hreg<Y::maskA()>(w);
+  if (valid) store_features_A<L>(a.phi + v.phi_off + 2 * off, lam, w, pl.Cs + off);
+  __syncwarp();
+}
+
+// One block item (11 <= L <= 14) on a sub-block of T threads with barrier `bar`.
+template <int L>
+__device__ void block_item(const GArgs& a, const GItem& it, float* buf, int lam, int bar) {
+  using Y = Lay<L>;
+  constexpr int d = Y::d, T = Y::T;
+  const GPlan pl = a.plans[it.plan];
+  const GVec v = a.vecs[it.vec];
+  const int64_t off = (int64_t)it.e * d;
+  const uint32_t buf_addr = smem_addr(buf);
+  float w[32];
+  load_row_A<L>(a.x + v.x_off, v.in_dim, a.vec_x, true, lam, w);
+  uint32_t mask = 0;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int k0 = Y::kA(lam, 4 * m);
+    mask |= ((__ldg(pl.bits + (int64_t)it.e * (d / 32) + (k0 >> 5)) >> (k0 & 31)) & 0xFu) << (4 * m);
+  }
+  apply_signs(w, mask);
+  hreg<Y::maskA()>(w);
+  store_A<L>(buf, 0, lam, w);
+  named_barrier(bar, T);
+  load_B<L>(buf, 0, lam, w);
+  hreg<Y::maskB()>(w);
+  store_B<L>(buf, 0, lam, w);
+  named_barrier(bar, T);
+  load_C<L>(buf, lam, w);
+  hreg<Y::maskC()>(w);
+  store_C<L>(buf, lam, w);
+  named_barrier(bar, T);
+  float gt[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const int k = Y::kC(lam, j);
+    gt[j] = __ldg(pl.G + off + k);
+    w[j] = lds32(buf_addr + 4u * (uint32_t)spos<L>(0, (int)__ldg(pl.perm + off + k)));
+  }
+  hreg_scaled<Y::maskC()>(w, gt);
+  named_barrier(bar, T);
+  store_C<L>(buf, lam, w);
+  named_barrier(bar, T);
+  load_B<L>(buf, 0, lam, w);
+  hreg<Y::maskB()>(w);
+  store_B<L>(buf, 0, lam, w);
+  named_barrier(bar, T);
+  load_A<L>(buf, 0, lam, w);
+  hreg<Y::maskA()>(w);
+  store_features_A<L>(a.phi + v.phi_off + 2 * off, lam, w, pl.Cs + off);
+  named_barrier(bar, T);
+}
+
+__global__ void __launch_bounds__(kGThreads, 1) k_grouped(const GArgs a) {
+  extern __shared__ float4 sm4[];
+  float* smem = reinterpret_cast<float*>(sm4);
+  __shared__ int s_unit;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (;;) {
+    if (threadIdx.x == 0) s_unit = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int64_t u = s_unit;
+    if (u >= a.num_units) break;
+    const GUnit unit = a.units[u];
+    if (unit.type == 0) {
+      float* buf = smem + warp * kWarpBuf;
+      for (int s = warp; s < unit.count; s += kGWarps) {
+        const GStep st = a.steps[unit.begin + s];
+        switch (st.L) {
+          case 5: warp_step<5>(a, st, buf, lane); break;
+          case 6: warp_step<6>(a, st, buf, lane); break;
+          case 7: warp_step<7>(a, st, buf, lane); break;
+          case 8: warp_step<8>(a, st, buf, lane); break;
+          case 9: warp_step<9>(a, st, buf, lane); break;
+          case 10: warp_step<10>(a, st, buf, lane); break;
+          default: break;
+        }
+      }
+    } else {
+      const int T = 1 << (unit.L - 5);
+      const int sb = threadIdx.x / T, lam = threadIdx.x % T;
+      if (sb < unit.count) {
+        const GItem it = a.items[unit.begin + sb];
+        const int slot = (1 << unit.L) + (1 << unit.L) / 32;
+        float* buf = smem + sb * slot;
+        switch (unit.L) {
+          case 11: block_item<11>(a, it, buf, lam, 1 + sb); break;
+          case 12: block_item<12>(a, it, buf, lam, 1 + sb); break;
+          case 13: block_item<13>(a, it, buf, lam, 1 + sb); break;
+          case 14: block_item<14>(a, it, buf, lam, 1 + sb); break;
+          default: break;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+double unit_cost(int L, int64_t vectors) { return (double)vectors * (double)(L + 4) * (1 << L); }
+
+}  // namespace
+}  // namespace mck
+
+using namespace mck;
+
+struct mck_group_s {
+  int device = 0;
+  int num_sms = 1;
+  int64_t x_len = 0, phi_len = 0;
+  bool vec_x = true;
+  int grain = 2;
+  std::vector<GPlan> plans;
+  std::vector<GVec> vecs;
+  std::vector<GStep> steps;
+  std::vector<int32_t> step_vecs;
+  std::vector<GItem> items;
+  std::vector<GUnit> units;
+  // device copies
+  GPlan* d_plans = nullptr;
+  GVec* d_vecs = nullptr;
+  GStep* d_steps = nullptr;
+  int32_t* d_step_vecs = nullptr;
+  GItem* d_items = nullptr;
+  GUnit* d_units = nullptr;
+  int* d_counter = nullptr;
+};
+
+namespace {
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& src) {
+  if (src.empty()) return cudaSuccess;
+  cudaError_t err = cudaMalloc(dst, sizeof(T) * src.size());
+  if (err != cudaSuccess) return err;
+  return cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+}
+
+void free_group_device(mck_group_s* g) {
+  cudaFree(g->d_plans);
+  cudaFree(g->d_vecs);
+  cudaFree(g->d_steps);
+  cudaFree(g->d_step_vecs);
+  cudaFree(g->d_items);
+  cudaFree(g->d_units);
+  cudaFree(g->d_counter);
+  cudaGetLastError();
+}
+
+// Units for the current grain, ordered by cost (largest first).
+void build_units(mck_group_s* g) {
+  struct U {
+    GUnit u;
+    double cost;
+  };
+  std::vector<U> list;
+  // warp steps, grouped by L so a unit's warps do similar work
+  std::vector<int64_t> order(g->steps.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int64_t)i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int64_t a, int64_t b) { return g->steps[a].L > g->steps[b].L; });
+  std::vector<GStep> sorted(g->steps.size());
+  for (size_t i = 0; i < order.size(); ++i) sorted[i] = g->steps[order[i]];
+  g->steps.swap(sorted);
+  const int per_unit = kGWarps * std::max(1, g->grain);
+  for (int64_t b = 0; b < (int64_t)g->steps.size(); b += per_unit) {
+    const int cnt = (int)std::min<int64_t>(per_unit, (int64_t)g->steps.size() - b);
+    double cost = 0.0;
+    for (int i = 0; i < cnt; ++i) cost += unit_cost(g->steps[b + i].L, g->steps[b + i].count);
+    list.push_back({GUnit{b, 0, 0, cnt, 0}, cost / kGWarps});
+  }
+  // block items: all items of one L are contiguous (sorted at create time)
+  int64_t b = 0;
+  while (b < (int64_t)g->items.size()) {
+    const int L = g->items[b].L;
+    const int per = kGThreads >> (L - 5);
+    int cnt = 0;
+    while (cnt < per && b + cnt < (int64_t)g->items.size() && g->items[b + cnt].L == L) ++cnt;
+    list.push_back({GUnit{b, 1, L, cnt, 0}, unit_cost(L, 1)});
+    b += cnt;
+  }
+  std::stable_sort(list.begin(), list.end(), [](const U& x, const U& y) { return x.cost > y.cost; });
+  g->units.clear();
+  for (const U& x : list) g->units.push_back(x.u);
+}
+
+mck_status_t upload_all(mck_group_s* g) {
+  free_group_device(g);
+  g->d_plans = nullptr;
+  g->d_vecs = nullptr;
+  g->d_steps = nullptr;
+  g->d_step_vecs = nullptr;
+  g->d_items = nullptr;
+  g->d_units = nullptr;
+  g->d_counter = nullptr;
+  cudaError_t err = upload(&g->d_plans, g->plans);
+  if (err == cudaSuccess) err = upload(&g->d_vecs, g->vecs);
+  if (err == cudaSuccess) err = upload(&g->d_steps, g->steps);
+  if (err == cudaSuccess) err = upload(&g->d_step_vecs, g->step_vecs);
+  if (err == cudaSuccess) err = upload(&g->d_items, g->items);
+  if (err == cudaSuccess) err = upload(&g->d_units, g->units);
+  if (err == cudaSuccess) err = cudaMalloc(&g->d_counter, sizeof(int));
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MCK_ENOMEM, "group work list upload failed");
+  }
+  return MCK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mck_status_t mck_group_create(mck_group_t* out, const mck_plan_t* plans, int32_t num_plans,
+                              const mck_group_item_t* items, int64_t num_items, int64_t x_len,
+                              int64_t phi_len, int32_t grain) {
+  if (!out || !plans || (num_items > 0 && !items)) return fail(MCK_EINVAL, "NULL argument");
+  if (num_plans < 1 || num_items < 0) return fail(MCK_EINVAL, "need >= 1 plan and >= 0 items");
+  if (num_items > (int64_t)1 << 30) return fail(MCK_EINVAL, "too many items");
+  if (grain < 0 || grain > 64) return fail(MCK_EINVAL, "grain must be in [0, 64]");
+  const int device = plans[0] ? plans[0]->device : 0;
+  for (int32_t p = 0; p < num_plans; ++p) {
+    if (!plans[p]) return fail(MCK_EINVAL, "NULL plan");
+    if (plans[p]->device != device) return fail(MCK_EINVAL, "plans on different devices");
+    if (plans[p]->L < 5 || plans[p]->L > 14)
+      return fail(MCK_EUNSUPPORTED, "grouped launches support 32 <= d <= 2^14");
+  }
+  mck_group_s* g = new (std::nothrow) mck_group_s();
+  if (!g) return fail(MCK_ENOMEM, "group allocation failed");
+  g->device = device;
+  g->num_sms = plans[0]->num_sms;
+  g->x_len = x_len;
+  g->phi_len = phi_len;
+  g->grain = grain ? grain : 2;
+  for (int32_t p = 0; p < num_plans; ++p) {
+    const mck_plan_s* q = plans[p];
+    g->plans.push_back(GPlan{q->permB, q->GB, q->maskA, q->Cs, q->B_bits, q->perm, q->G, q->L, q->E});
+  }
+  // per-plan vector lists (for warp steps) and validation
+  std::vector<std::vector<int32_t>> by_plan(num_plans);
+  for (int64_t i = 0; i < num_items; ++i) {
+    const mck_group_item_t& it = items[i];
+    if (it.plan < 0 || it.plan >= num_plans) {
+      delete g;
+      return fail(MCK_EINVAL, "item " + std::to_string(i) + ": plan index out of range");
+    }
+    const mck_plan_s* q = plans[it.plan];
+    if (it.E < 1 || it.E > q->E || it.in_dim < 1 || it.in_dim > q->d || it.x_offset < 0 ||
+        it.phi_offset < 0 || it.x_offset + it.in_dim > x_len ||
+        it.phi_offset + 2 * (int64_t)it.E * q->d > phi_len) {
+      delete g;
+      return fail(MCK_EINVAL, "item " + std::to_string(i) + ": E, in_dim or offsets out of range");
+    }
+    if ((it.phi_offset & 3) != 0) {
+      delete g;
+      return fail(MCK_EINVAL, "item " + std::to_string(i) + ": phi_offset must be a multiple of 4");
+    }
+    if ((it.x_offset & 3) || (it.in_dim & 3)) g->vec_x = false;
+    g->vecs.push_back(GVec{it.x_offset, it.phi_offset, (int32_t)it.in_dim, it.E});
+    by_plan[it.plan].push_back((int32_t)i);
+  }
+  for (int32_t p = 0; p < num_plans; ++p) {
+    const int L = plans[p]->L;
+    std::vector<int32_t>& vs = by_plan[p];
+    std::stable_sort(vs.begin(), vs.end(),
+                     [&](int32_t a, int32_t b) { return g->vecs[a].E > g->vecs[b].E; });
+    if (L <= 10) {
+      const int vpw = 32 >> (L - 5);
+      const int emax = vs.empty() ? 0 : g->vecs[vs[0]].E;
+      for (int e = 0; e < emax; ++e) {
+        int64_t cnt = 0;  // vectors using expansion e: a prefix of vs
+        while (cnt < (int64_t)vs.size() && g->vecs[vs[cnt]].E > e) ++cnt;
+        for (int64_t b = 0; b < cnt; b += vpw) {
+          const int c = (int)std::min<int64_t>(vpw, cnt - b);
+          g->steps.push_back(GStep{(int64_t)g->step_vecs.size(), p, e, L, c});
+          for (int k = 0; k < c; ++k) g->step_vecs.push_back(vs[b + k]);
+        }
+      }
+    } else {
+      for (int32_t v : vs)
+        for (int e = 0; e < g->vecs[v].E; ++e) g->items.push_back(GItem{v, p, e, L});
+    }
+  }
+  std::stable_sort(g->items.begin(), g->items.end(),
+                   [](const GItem& a, const GItem& b) { return a.L > b.L; });
+  build_units(g);
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(device);
+  mck_status_t st = upload_all(g);
+  if (st == MCK_OK) {
+    cudaError_t err = cudaFuncSetAttribute(k_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(float) * kSmemFloats));
+    if (err != cudaSuccess) st = cuda_fail(err, "mck_group_create");
+  }
+  if (prev >= 0) cudaSetDevice(prev);
+  if (st != MCK_OK) {
+    free_group_device(g);
+    delete g;
+    return st;
+  }
+  *out = g;
+  return MCK_OK;
+}
+
+mck_status_t mck_group_set_grain(mck_group_t g, int32_t grain) {
+  if (!g) return fail(MCK_EINVAL, "group is NULL");
+  if (grain < 1 || grain > 64) return fail(MCK_EINVAL, "grain must be in [1, 64]");
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(g->device);
+  cudaDeviceSynchronize();  // no queued launch may still read the old unit list
+  g->grain = grain;
+  build_units(g);
+  cudaFree(g->d_units);
+  g->d_units = nullptr;
+  cudaFree(g->d_steps);
+  g->d_steps = nullptr;
+  cudaError_t err = upload(&g->d_steps, g->steps);
+  if (err == cudaSuccess) err = upload(&g->d_units, g->units);
+  if (prev >= 0) cudaSetDevice(prev);
+  return err == cudaSuccess ? MCK_OK : cuda_fail(err, "mck_group_set_grain");
+}
+
+mck_status_t mck_group_info(mck_group_t g, int64_t* num_units, int64_t* num_steps,
+                            int64_t* num_block_items, int32_t* grain) {
+  if (!g) return fail(MCK_EINVAL, "group is NULL");
+  if (num_units) *num_units = (int64_t)g->units.size();
+  if (num_steps) *num_steps = (int64_t)g->steps.size();
+  if (num_block_items) *num_block_items = (int64_t)g->items.size();
+  if (grain) *grain = g->grain;
+  return MCK_OK;
+}
+
+void mck_group_destroy(mck_group_t g) {
+  if (!g) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(g->device);
+  cudaDeviceSynchronize();
+  free_group_device(g);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete g;
+}
+
+mck_status_t mck_group_features(mck_group_t g, const float* x, float* phi, mck_stream_t stream) {
+  if (!g) return fail(MCK_EINVAL, "group is NULL");
+  if (g->units.empty()) return MCK_OK;
+  if (!x || !phi) return fail(MCK_EINVAL, "x and phi must not be NULL");
+  if ((uintptr_t)phi % 16) return fail(MCK_EINVAL, "phi must be 16-byte aligned");
+  mck_status_t st = check_device_array(x, 4 * g->x_len, g->device, "x");
+  if (st == MCK_OK) st = check_device_array(phi, 4 * g->phi_len, g->device, "phi");
+  if (st != MCK_OK) return st;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != g->device) cudaSetDevice(g->device);
+  GArgs a{};
+  a.plans = g->d_plans;
+  a.vecs = g->d_vecs;
+  a.steps = g->d_steps;
+  a.step_vecs = g->d_step_vecs;
+  a.items = g->d_items;
+  a.units = g->d_units;
+  a.num_units = (int64_t)g->units.size();
+  a.counter = g->d_counter;
+  a.x = x;
+  a.phi = phi;
+  a.vec_x = g->vec_x && ((uintptr_t)x % 16 == 0);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t err = cudaMemsetAsync(g->d_counter, 0, sizeof(int), s);
+  if (err == cudaSuccess) {
+    const unsigned grid = (unsigned)std::max(1, std::min<int>(g->num_sms, (int)g->units.size()));
+    k_grouped<<<grid, kGThreads, sizeof(float) * kSmemFloats, s>>>(a);
+    err = cudaGetLastError();
+  }
+  if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
+  return err == cudaSuccess ? MCK_OK : cuda_fail(err, "mck_group_features");
+}
+
+}  // extern "C"

@@ -36,6 +36,8 @@ namespace mck {
 // Thread-local error message; returns the status for convenient `return fail(...)`.
 mck_status_t fail(mck_status_t s, const std::string& msg);
 mck_status_t cuda_fail(cudaError_t err, const char* where);
+// `p` must be device memory of `device` whose allocation holds [p, p + bytes).
+mck_status_t check_device_array(const void* p, int64_t bytes, int device, const char* name);
 
 // ---- plan.cu -------------------------------------------------------------
 mck_status_t build_tables(mck_plan_s* p, cudaStream_t s);
