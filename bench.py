@@ -22,6 +22,8 @@ Reported:
   fwht_sweep   config 2: the standalone transform over 1 GiB batches, d = 2^10..2^20
   uneven_batch config 4: 10000 vectors of mixed d, E and kernel in one persistent
                graph-launched kernel vs one launch per (d, E, kernel) class
+  configs01    config 0 (256-row latency check) and config 1 (60000 rows, E=8,
+               RBF and Matern features and fused logits)
   cpu_baseline the FP64 oracle on a bounded sample of the same workload
 
 --impl reference times the oracle itself (CPU) on the same workload, as the
@@ -300,6 +302,7 @@ def main():
         line["train_step"] = train_step_leg(mck, dev, stream, args)
         line["fwht_sweep"] = fwht_sweep_leg(mck, dev, stream, args)
         line["uneven_batch"] = uneven_leg(mck, dev, stream, args)
+        line["configs01"] = configs01_leg(mck, dev, stream, args)
     del phi
     if rank == 0 and world == 1 and not args.no_extras:
         line["cpu_baseline"] = cpu_baseline()
@@ -441,6 +444,53 @@ def fwht_sweep_leg(mck, dev, stream, args):
                    "max_err_rel_sqrt_d_rms": rel})
     del work, x0
     return {"dtype": "f32", "elements_per_d": total, "sizes": out, "tensor_core_d1024": tc}
+
+
+def configs01_leg(mck, dev, stream, args):
+    """Config 0 (256 rows, E=1, sigma=1: a latency check) and config 1 (60000
+    rows, E=8, sigma=3, RBF and Matern t=40; features and fused 10-class logits)."""
+    import torch
+
+    import workloads as wl
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        e.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(e) / reps
+
+    out = {}
+    p0 = mck.Plan(D, 1, "rbf", 1.0, SEED)
+    x0 = torch.from_numpy(wl.mnist_like(256, IN_DIM, seed=SEED)).to(dev)
+    f0 = torch.empty((256, 2 * D), device=dev)
+    ms = timed(lambda: mck.features(p0, x0, out=f0), 20)
+    out["config0"] = {"rows": 256, "E": 1, "ms": ms, "features_per_s": 256 * 2 * D / (ms / 1e3)}
+    p0.close()
+    x1 = torch.from_numpy(wl.mnist_like(N, IN_DIM, seed=SEED)).to(dev)
+    E1, F1 = 8, 2 * 8 * D
+    f1 = torch.empty((N, F1), device=dev)
+    W, b = wl.logit_weights(C, F1, seed=SEED)
+    Wd, bd = torch.from_numpy(W).to(dev), torch.from_numpy(b).to(dev)
+    lo = torch.empty((N, C), device=dev)
+    peak, _ = measured_peaks()
+    for kern in ("rbf", "matern"):
+        pl = mck.Plan(D, E1, kern, 3.0, SEED, matern_t=40)
+        ms = timed(lambda: mck.features(pl, x1, out=f1), max(3, args.steps // 5))
+        ml = timed(lambda: mck.fused_logits(pl, x1, Wd, bd, out=lo), 3)
+        gbs = N * (IN_DIM * 4 + F1 * 4) / (ms / 1e3) / 1e9
+        out[f"config1_{kern}"] = {"rows": N, "E": E1, "sigma": 3.0, "ms_features": ms,
+                                  "features_per_s": N * F1 / (ms / 1e3), "gbs": gbs,
+                                  "frac_of_measured_hbm": gbs / peak,
+                                  "ms_fused_logits": ml, "logit_rows_per_s": N / (ml / 1e3)}
+        pl.close()
+    del f1, x1
+    return out
 
 
 def uneven_leg(mck, dev, stream, args):

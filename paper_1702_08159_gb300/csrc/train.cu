@@ -383,23 +383,43 @@ __global__ void k_reduce_params(const float* __restrict__ partials, int64_t d, i
   if (dG) dG[t] = s2;
 }
 
-// dW[c][f] = sum_n dlogits[n][c] phi[n][f]; db[c] = sum_n dlogits[n][c].
-__global__ void k_weight_grads(const float* __restrict__ dl, const float* __restrict__ phi,
-                               int64_t n, int C, int64_t F, float* __restrict__ dW) {
-  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= F) return;
+// dW[c][f] = sum_n dlogits[n][c] phi[n][f]. A block owns 32 consecutive
+// columns; its 8 warps take the rows n = w, w + 8, ... (one column per lane,
+// coalesced 128-byte row segments) and the 8 partial sums are added in warp
+// order through shared memory, so the result does not depend on scheduling.
+constexpr int kWgRowGroups = 8;
+
+__global__ void __launch_bounds__(32 * kWgRowGroups) k_weight_grads(const float* __restrict__ dl,
+                                                                   const float* __restrict__ phi,
+                                                                   int64_t n, int C, int64_t F,
+                                                                   float* __restrict__ dW) {
+  __shared__ float part[kWgRowGroups][CMAX][32];
+  const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;
+  const int64_t f = (int64_t)blockIdx.x * 32 + lane;
   float acc[CMAX];
 #pragma unroll
   for (int c = 0; c < CMAX; ++c) acc[c] = 0.f;
-  for (int64_t i = 0; i < n; ++i) {
-    const float p = phi[i * F + f];
+  if (f < F) {
+    for (int64_t i = rg; i < n; i += kWgRowGroups) {
+      const float p = phi[i * F + f];
 #pragma unroll
-    for (int c = 0; c < CMAX; ++c)
-      if (c < C) acc[c] = fmaf(__ldg(dl + i * C + c), p, acc[c]);
+      for (int c = 0; c < CMAX; ++c)
+        if (c < C) acc[c] = fmaf(__ldg(dl + i * C + c), p, acc[c]);
+    }
   }
 #pragma unroll
-  for (int c = 0; c < CMAX; ++c)
-    if (c < C) dW[c * F + f] = acc[c];
+  for (int c = 0; c < CMAX; ++c) part[rg][c][lane] = acc[c];
+  __syncthreads();
+  if (rg == 0 && f < F) {
+#pragma unroll
+    for (int c = 0; c < CMAX; ++c) {
+      if (c < C) {
+        float t = 0.f;
+        for (int q = 0; q < kWgRowGroups; ++q) t += part[q][c][lane];
+        dW[c * F + f] = t;
+      }
+    }
+  }
 }
 
 __global__ void k_bias_grads(const float* __restrict__ dl, int64_t n, int C, float* __restrict__ db) {
@@ -485,7 +505,7 @@ cudaError_t launch_backward(const BackwardArgs& b, float* partials, int64_t num_
 cudaError_t launch_logit_weight_grads(const float* dlogits, const float* phi, int64_t n, int C,
                                       int64_t F, float* dW, float* db, cudaStream_t s) {
   if (dW) {
-    k_weight_grads<<<(unsigned)((F + 255) / 256), 256, 0, s>>>(dlogits, phi, n, C, F, dW);
+    k_weight_grads<<<(unsigned)((F + 31) / 32), 32 * kWgRowGroups, 0, s>>>(dlogits, phi, n, C, F, dW);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
