@@ -439,7 +439,7 @@ mck_status_t mck_fused_logits(mck_plan_t p, const float* x, int64_t n, int64_t i
   MCK_TRY(check_array(logits, 4 * n * C, p->device, "logits"));
   cudaStream_t s = (cudaStream_t)stream;
   Scratch part(s);
-  MCK_TRY(part.alloc(sizeof(float) * (size_t)n * p->E * C));
+  if (logits_need_scratch(p->L)) MCK_TRY(part.alloc(sizeof(float) * (size_t)n * p->E * C));
   return launched(launch_logits(feature_args(p, x, n, in_dim, ldx, Cs, G), W, b, C,
                                 (float*)part.ptr, logits, s),
                   "mck_fused_logits");

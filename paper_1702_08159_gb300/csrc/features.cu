@@ -446,6 +446,175 @@ __global__ void __launch_bounds__(128) k_feat_tiny(const Launch P) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fused logits at d = 1024: a block of 8 warps owns a tile of 8 rows. For each
+// expansion every warp computes its row's 2048 features (the feature kernel's
+// sequence) into a shared 8 x 2048 tile; then the 256 threads contract the
+// tile with W: thread (class group cg, feature thread ft) owns classes
+// [cg*CPT, cg*CPT + CPT) and features ft, ft + TPG, ... for all 8 rows, so
+// each weight is loaded once per 8 rows. Partial sums stay in registers over
+// all expansions and are reduced once per tile in a fixed order.
+// ---------------------------------------------------------------------------
+constexpr int kTileRows = 8;
+
+template <int CPT>
+__global__ void __launch_bounds__(kTileRows * 32, 1) k_logits_tile(const Launch P,
+                                                                    const float* __restrict__ b,
+                                                                    float* __restrict__ logits) {
+  constexpr int L = 10;
+  using Y = Lay<L>;
+  constexpr int d = Y::d, F2 = 2 * d;
+  extern __shared__ float4 sm4[];
+  float* phis = reinterpret_cast<float*>(sm4);        // [kTileRows][F2]
+  float* bufs = phis + kTileRows * F2;                 // [kTileRows][SLOT]
+  float* red = bufs + kTileRows * Y::SLOT;             // [8 warps][kTileRows][CPT] reduction
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* buf = bufs + warp * Y::SLOT;
+  const uint32_t slot = smem_addr(buf);
+  const int C = P.C, E = P.a.E;
+  const int CG = (C + CPT - 1) / CPT;                  // class groups (1 or 2)
+  const int TPG = (kTileRows * 32) / CG;               // threads per group
+  const int cg = threadIdx.x / TPG, ft = threadIdx.x % TPG;
+  const int64_t F = 2ll * E * d;
+  const int64_t tiles = (P.a.n + kTileRows - 1) / kTileRows;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    float acc[kTileRows][CPT];
+#pragma unroll
+    for (int s = 0; s < kTileRows; ++s)
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) acc[s][c] = 0.f;
+    const int64_t n = tile * kTileRows + warp;
+    const bool valid = n < P.a.n;
+    for (int e = 0; e < E; ++e) {
+      const int64_t off = (int64_t)e * d;
+      // ---- features of row n, expansion e -> phis[warp][.] ----
+      {
+        const uint32_t bmask = __ldg(P.a.maskA + (int64_t)e * Y::T + lane);
+        uint32_t poff[16];
+        float gt[32];
+        const uint4* pb = reinterpret_cast<const uint4*>(P.a.permB + off) + lane;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const uint4 v = __ldg(pb + m * Y::T);
+          poff[2 * m] = v.x | (v.y << 16);
+          poff[2 * m + 1] = v.z | (v.w << 16);
+        }
+        if (P.a.GB) {
+          const float4* gb = reinterpret_cast<const float4*>(P.a.GB + off) + lane;
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            const float4 v = __ldg(gb + m * Y::T);
+            gt[4 * m] = v.x;
+            gt[4 * m + 1] = v.y;
+            gt[4 * m + 2] = v.z;
+            gt[4 * m + 3] = v.w;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) gt[j] = __ldg(P.a.G + off + Y::kB(lane, j));
+        }
+        float w[32];
+        load_x_A<L>(P, n, valid, lane, w);
+        apply_signs(w, bmask);
+        hreg<Y::maskA()>(w);
+        store_A<L>(buf, 0, lane, w);
+        __syncwarp();
+        load_B<L>(buf, 0, lane, w);
+        hreg<Y::maskB()>(w);
+        store_B<L>(buf, 0, lane, w);
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          w[j] = lds32(slot + ((j & 1) ? (poff[j >> 1] >> 16) : (poff[j >> 1] & 0xffffu)));
+        hreg_scaled<Y::maskB()>(w, gt);
+        __syncwarp();
+        store_B<L>(buf, 0, lane, w);
+        __syncwarp();
+        load_A<L>(buf, 0, lane, w);
+        hreg<Y::maskA()>(w);
+        float* ph = phis + warp * F2;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int k0 = Y::kA(lane, 4 * m);
+          const float4 c4 = __ldg(reinterpret_cast<const float4*>(P.a.Cs + off + k0));
+          const float cs[4] = {c4.x, c4.y, c4.z, c4.w};
+          float c[4], s4[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) cos_sin(cs[q] * w[4 * m + q], c[q], s4[q]);
+          // an invalid row contributes nothing
+          if (!valid) c[0] = c[1] = c[2] = c[3] = s4[0] = s4[1] = s4[2] = s4[3] = 0.f;
+          *reinterpret_cast<float4*>(ph + k0) = make_float4(c[0], c[1], c[2], c[3]);
+          *reinterpret_cast<float4*>(ph + d + k0) = make_float4(s4[0], s4[1], s4[2], s4[3]);
+        }
+      }
+      __syncthreads();
+      // ---- contraction of the 8-row tile with W_e ----
+      const float* Wg = P.W + (int64_t)(cg * CPT) * F + 2ll * e * d;
+      for (int f = ft; f < F2; f += TPG) {
+        float p[kTileRows];
+#pragma unroll
+        for (int s = 0; s < kTileRows; ++s) p[s] = phis[s * F2 + f];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          if (cg * CPT + c < C) {
+            const float wv = __ldg(Wg + c * F + f);
+#pragma unroll
+            for (int s = 0; s < kTileRows; ++s) acc[s][c] = fmaf(wv, p[s], acc[s][c]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // ---- reduce over the TPG threads of each class group (fixed order) ----
+#pragma unroll
+    for (int s = 0; s < kTileRows; ++s)
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        float t = acc[s][c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        acc[s][c] = t;
+      }
+    if (lane == 0) {
+#pragma unroll
+      for (int s = 0; s < kTileRows; ++s)
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) red[(warp * kTileRows + s) * CPT + c] = acc[s][c];
+    }
+    __syncthreads();
+    const int wpg = TPG / 32;  // warps per class group
+    for (int o = threadIdx.x; o < kTileRows * C; o += blockDim.x) {
+      const int s = o / C, cls = o % C;
+      const int g2 = cls / CPT, c = cls % CPT;
+      float t = 0.f;
+      for (int q = 0; q < wpg; ++q) t += red[((g2 * wpg + q) * kTileRows + s) * CPT + c];
+      const int64_t row = tile * kTileRows + s;
+      if (row < P.a.n) logits[row * C + cls] = t + (b ? b[cls] : 0.f);
+    }
+    __syncthreads();
+  }
+}
+
+template <int CPT>
+cudaError_t run_logits_tile(const Launch& P, const float* b, float* logits, cudaStream_t s) {
+  using Y = Lay<10>;
+  const size_t smem = sizeof(float) * (kTileRows * 2 * Y::d + kTileRows * Y::SLOT +
+                                       kTileRows * kTileRows * CPT);
+  cudaError_t err = cudaFuncSetAttribute(k_logits_tile<CPT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_logits_tile<CPT>, kTileRows * 32,
+                                                    smem) != cudaSuccess)
+    occ = 1;
+  occ = std::max(occ, 1);
+  const int64_t tiles = (P.a.n + kTileRows - 1) / kTileRows;
+  const unsigned grid =
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)P.a.num_sms * occ));
+  k_logits_tile<CPT><<<grid, kTileRows * 32, smem, s>>>(P, b, logits);
+  return cudaGetLastError();
+}
+
 // logits[n][c] = b[c] + sum_e part[n][e][c], expansions summed in order.
 __global__ void k_logits_reduce(const float* __restrict__ part, const float* __restrict__ b,
                                 int64_t n, int E, int C, float* __restrict__ logits) {
@@ -532,6 +701,8 @@ cudaError_t launch_features(const FeatureArgs& a, float* phi, cudaStream_t s) {
   return dispatch<MODE_FEATURES>(P, s);
 }
 
+bool logits_need_scratch(int L) { return L != 10; }
+
 cudaError_t launch_logits(const FeatureArgs& a, const float* W, const float* b, int C,
                           float* part, float* logits, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
@@ -539,6 +710,19 @@ cudaError_t launch_logits(const FeatureArgs& a, const float* W, const float* b, 
   P.W = W;
   P.part = part;
   P.C = C;
+  if (a.L == 10) {  // tile kernel: logits written directly, no partials
+    const int cg = C <= 8 ? 1 : 2;
+    switch ((C + cg - 1) / cg) {
+      case 1: return run_logits_tile<1>(P, b, logits, s);
+      case 2: return run_logits_tile<2>(P, b, logits, s);
+      case 3: return run_logits_tile<3>(P, b, logits, s);
+      case 4: return run_logits_tile<4>(P, b, logits, s);
+      case 5: return run_logits_tile<5>(P, b, logits, s);
+      case 6: return run_logits_tile<6>(P, b, logits, s);
+      case 7: return run_logits_tile<7>(P, b, logits, s);
+      default: return run_logits_tile<8>(P, b, logits, s);
+    }
+  }
   cudaError_t err = dispatch<MODE_LOGITS>(P, s);
   if (err != cudaSuccess) return err;
   const int64_t total = a.n * C;

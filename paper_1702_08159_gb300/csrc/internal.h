@@ -69,6 +69,8 @@ struct FeatureArgs {
 
 cudaError_t launch_features(const FeatureArgs& a, float* phi, cudaStream_t s);
 // Partial logits per (sample, expansion): part is n x E x C; then logits = sum_e part + b.
+// At d = 1024 the tile kernel writes logits directly and `part` is unused.
+bool logits_need_scratch(int L);
 cudaError_t launch_logits(const FeatureArgs& a, const float* W, const float* b, int C,
                           float* part, float* logits, cudaStream_t s);
 

@@ -26,7 +26,8 @@ def _rel(got, ref):
 
 
 @pytest.mark.parametrize("d,E,C,n", [(8, 2, 10, 5), (64, 2, 3, 9), (1024, 2, 10, 17),
-                                     (1024, 3, 16, 8), (2048, 1, 1, 3), (256, 4, 7, 33)])
+                                     (1024, 3, 16, 8), (1024, 2, 1, 9), (1024, 2, 9, 23),
+                                     (1024, 1, 8, 1), (2048, 1, 1, 3), (256, 4, 7, 33)])
 def test_fused_logits(mck, dev, d, E, C, n):
     plan = mck.Plan(d, E, "rbf", 1.0, 3)
     x = wl.mnist_like(n, min(d, 784), seed=d)

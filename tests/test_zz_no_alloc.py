@@ -34,12 +34,14 @@ def test_noalloc_matches_allocating_entry_point_twice(mck, dev):
     from paper_1702_08159_gb300 import _lib
 
     lib = _lib.load()
-    plan = mck.Plan(1024, 4, "rbf", 1.0, 42)
+    # d = 512 runs the fused-logits path that keeps per-(sample, expansion)
+    # partial logits in scratch (d = 1024 reduces inside the kernel instead).
+    plan = mck.Plan(512, 4, "rbf", 1.0, 42)
     C = 10
     W = torch.from_numpy(wl.logit_weights(C, plan.num_features, seed=3, std=0.05)[0]).to(dev)
     b = torch.linspace(-1, 1, C, device=dev)
     for call, (n, seed) in enumerate([(1000, 1), (333, 2)]):
-        x = torch.from_numpy(wl.mnist_like(n, 784, seed=seed)).to(dev)
+        x = torch.from_numpy(wl.mnist_like(n, 500, seed=seed)).to(dev)
         ref = torch.empty((n, C), device=dev)
         got = torch.full((n, C), float("nan"), device=dev)
         assert _call(lib, "mck_fused_logits", plan, x, W, b, ref) == 0
