@@ -62,6 +62,10 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip train_step/fused_logits/e2e/cpu legs")
     p.add_argument("--batch", type=int, default=N,
                    help="rows per GPU (default 60000; smaller values are for profiling captures)")
+    p.add_argument("--legs", default="all",
+                   help="comma list of extra legs to run (e2e,logits,train,sweep,uneven,configs01) or 'all'")
+    p.add_argument("--uneven-count", type=int, default=10000,
+                   help="vectors in the config-4 leg (smaller values are for profiling captures)")
     return p.parse_args()
 
 
@@ -297,12 +301,20 @@ def main():
                           "max": max(launch_ms)}}
 
     if not args.no_extras:
-        line["e2e"] = e2e_leg(mck, plan, x_host, dev, stream, world)
-        line["fused_logits"] = fused_logits_leg(mck, plan, x, dev, stream, args)
-        line["train_step"] = train_step_leg(mck, dev, stream, args)
-        line["fwht_sweep"] = fwht_sweep_leg(mck, dev, stream, args)
-        line["uneven_batch"] = uneven_leg(mck, dev, stream, args)
-        line["configs01"] = configs01_leg(mck, dev, stream, args)
+        legs = set(args.legs.split(",")) if args.legs != "all" else {
+            "e2e", "logits", "train", "sweep", "uneven", "configs01"}
+        if "e2e" in legs:
+            line["e2e"] = e2e_leg(mck, plan, x_host, dev, stream, world)
+        if "logits" in legs:
+            line["fused_logits"] = fused_logits_leg(mck, plan, x, dev, stream, args)
+        if "train" in legs:
+            line["train_step"] = train_step_leg(mck, dev, stream, args)
+        if "sweep" in legs:
+            line["fwht_sweep"] = fwht_sweep_leg(mck, dev, stream, args)
+        if "uneven" in legs:
+            line["uneven_batch"] = uneven_leg(mck, dev, stream, args)
+        if "configs01" in legs:
+            line["configs01"] = configs01_leg(mck, dev, stream, args)
     del phi
     if rank == 0 and world == 1 and not args.no_extras:
         line["cpu_baseline"] = cpu_baseline()
@@ -503,7 +515,7 @@ def uneven_leg(mck, dev, stream, args):
     import workloads as wl
     from paper_1702_08159_gb300.tune import tune_grain
 
-    b = wl.uneven_batch(10000, seed=SEED)
+    b = wl.uneven_batch(args.uneven_count, seed=SEED)
     keys = sorted(set(zip(b["d"].tolist(), b["kernel"].tolist())))
     plans = [mck.Plan(d, 32, "rbf" if k == 0 else "matern", 1.0, SEED, matern_t=40)
              for d, k in keys]

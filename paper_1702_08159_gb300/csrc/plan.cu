@@ -107,12 +107,15 @@ __global__ void k_plan_rbf(float* __restrict__ Cs, const double* __restrict__ no
 // u_j = U_j^{1/d} X_j/||X_j||, X_j ~ N(0, I_d) (coordinates 2p, 2p+1 are the
 // Box-Muller pair of counter (p, e, 5 + 16k, j)), U_j = (w0+1)/2^32 of
 // counter (k, e, 6, j). One block per (e, k) (block index e*d + k); each thread owns up to 16 pairs
-// of coordinates of the running sum. X_j is drawn twice (once for its norm,
-// once to accumulate), which keeps the sum in registers. Float32 coordinates,
-// float64 norms.
+// of coordinates of the running sum, which stays in registers. Float32
+// coordinates; squared norms summed in float per thread and in float64 across
+// threads.
 constexpr int kBallPairs = 16;
 
-__global__ void __launch_bounds__(1024) k_plan_matern(float* __restrict__ Cs,
+// KEEP: each thread keeps its coordinates of X_j in registers between the
+// norm and the accumulation (up to 512 threads); otherwise X_j is drawn twice.
+template <bool KEEP>
+__global__ void __launch_bounds__(KEEP ? 512 : 1024) k_plan_matern(float* __restrict__ Cs,
                                                       const double* __restrict__ norm, int64_t d,
                                                       int32_t t_order, double inv_sigma_sqrt_d,
                                                       uint32_t k0, uint32_t k1) {
@@ -151,18 +154,24 @@ __global__ void __launch_bounds__(1024) k_plan_matern(float* __restrict__ Cs,
     xs = r * sn;
   };
 
+  float xk[KEEP ? 2 * kBallPairs : 1];
   for (uint32_t j = 1; j <= (uint32_t)t_order; ++j) {
-    double ss = 0.0;
+    // ||X_j||^2: float sums over a thread's (at most 32) coordinates, float64 across threads
+    float ssf = 0.f;
 #pragma unroll
     for (int i = 0; i < kBallPairs; ++i) {
       const int64_t p = tid + (int64_t)i * nt;
       if (p < pairs) {
         float xc, xs;
         coords(p, j, xc, xs);
-        ss += (double)xc * xc + (double)xs * xs;
+        if constexpr (KEEP) {
+          xk[2 * i] = xc;
+          xk[2 * i + 1] = xs;
+        }
+        ssf += xc * xc + xs * xs;
       }
     }
-    const double xnorm = sqrt(block_sum(ss));
+    const double xnorm = sqrt(block_sum((double)ssf));
     const U32x4 wr = philox4x32_10(k, e, kTagBallRadius, j, k0, k1);
     const double rho = pow(unit_open0(wr.x), 1.0 / (double)d);
     const float scale = (float)(rho / xnorm);
@@ -171,7 +180,12 @@ __global__ void __launch_bounds__(1024) k_plan_matern(float* __restrict__ Cs,
       const int64_t p = tid + (int64_t)i * nt;
       if (p < pairs) {
         float xc, xs;
-        coords(p, j, xc, xs);
+        if constexpr (KEEP) {
+          xc = xk[2 * i];
+          xs = xk[2 * i + 1];
+        } else {
+          coords(p, j, xc, xs);
+        }
         s[2 * i] = fmaf(scale, xc, s[2 * i]);
         s[2 * i + 1] = fmaf(scale, xs, s[2 * i + 1]);
       }
@@ -279,7 +293,10 @@ mck_status_t build_tables(mck_plan_s* p, cudaStream_t s) {
     const int64_t pairs = d / 2;
     int threads = (int)((pairs + kBallPairs - 1) / kBallPairs);
     threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : threads);
-    k_plan_matern<<<(unsigned)(d * E), threads, 0, s>>>(p->Cs, norm, d, p->matern_t, inv, k0, k1);
+    if (threads <= 512)
+      k_plan_matern<true><<<(unsigned)(d * E), threads, 0, s>>>(p->Cs, norm, d, p->matern_t, inv, k0, k1);
+    else
+      k_plan_matern<false><<<(unsigned)(d * E), threads, 0, s>>>(p->Cs, norm, d, p->matern_t, inv, k0, k1);
   }
   const size_t perm_smem = sizeof(uint32_t) * (size_t)(d + 1024);
   err = cudaFuncSetAttribute(k_plan_perm, cudaFuncAttributeMaxDynamicSharedMemorySize,
