@@ -366,7 +366,8 @@ def fused_logits_leg(mck, plan, x, dev, stream, args):
 
     W, b = wl.logit_weights(C, F, seed=SEED)
     Wd, bd = torch.from_numpy(W).to(dev), torch.from_numpy(b).to(dev)
-    out = torch.empty((N, C), device=dev)
+    n = x.shape[0]
+    out = torch.empty((n, C), device=dev)
     for _ in range(2):
         mck.fused_logits(plan, x, Wd, bd, out=out)
     torch.cuda.synchronize()
@@ -379,8 +380,8 @@ def fused_logits_leg(mck, plan, x, dev, stream, args):
     torch.cuda.synchronize()
     ms = a.elapsed_time(e) / steps
     # FP32 FMAs: features' transforms are not counted; the contraction is C*2Ed per row.
-    return {"samples_per_s": N / (ms / 1e3), "features_per_s": N * F / (ms / 1e3),
-            "ms_per_call": ms, "num_classes": C, "gpu_launches_per_call": 2}
+    return {"rows": n, "samples_per_s": n / (ms / 1e3), "features_per_s": n * F / (ms / 1e3),
+            "ms_per_call": ms, "num_classes": C, "gpu_launches_per_call": 1}
 
 
 def fwht_sweep_leg(mck, dev, stream, args):
@@ -619,7 +620,37 @@ def train_step_leg(mck, dev, stream, args):
         torch.cuda.synchronize()
         return a.elapsed_time(e) / steps
 
+    def graphed(step, params):
+        """The same step captured once in a CUDA graph (launch overhead removed)."""
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                step()  # leaves every parameter with a .grad to accumulate into
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for p in params:
+                p.grad.zero_()
+            step()
+        return g.replay
+
+    def fused_step():
+        model.loss(x, y).backward()
+
+    def plain_step():
+        phi = FastfoodFeatures.apply(plan, x, Cs, G)
+        torch.nn.functional.cross_entropy(phi @ Wp.T + bp, y.long()).backward()
+
     tf, tp = timed(fused), timed(plain)
+    graph = {}
+    try:
+        graph["ms_fused_graph"] = timed(graphed(fused_step, list(model.parameters())))
+        graph["ms_plain_graph"] = timed(graphed(plain_step, [Cs, G, Wp, bp]))
+        graph["speedup_vs_plain_graph"] = graph["ms_plain_graph"] / graph["ms_fused_graph"]
+    except Exception as exc:  # capture is an optional view of the same step
+        graph["graph_error"] = f"{type(exc).__name__}: {exc}"[:200]
     # equal accuracy: the two paths' gradients agree
     fused()
     plain()
@@ -627,7 +658,7 @@ def train_step_leg(mck, dev, stream, args):
     dmax = max(float((model.W.grad - Wp.grad).abs().max() / Wp.grad.abs().max()),
                float((model.G.grad - G.grad).abs().max() / G.grad.abs().max()))
     plan.close()
-    return {"batch": n, "ms_fused": tf, "ms_plain": tp, "speedup_vs_plain": tp / tf,
+    return {"batch": n, "ms_fused": tf, "ms_plain": tp, "speedup_vs_plain": tp / tf, **graph,
             "grad_rel_diff_fused_vs_plain": dmax,
             "plain": "mck_features + torch matmul + torch cross_entropy + mck_features_backward"}
 

@@ -152,7 +152,8 @@ mck_status_t mck_features_backward(mck_plan_t plan, const float* x, int64_t n, i
  *   b        device num_classes or NULL (zero bias)
  *   logits   device n x num_classes
  * 1 <= num_classes <= MCK_MAX_CLASSES. Uses stream-ordered scratch memory of
- * n x E x num_classes floats. */
+ * at most n x E x num_classes floats for partial logits (none at d = 1024
+ * when the batch has at least 8 rows per SM). */
 mck_status_t mck_fused_logits(mck_plan_t plan, const float* x, int64_t n, int64_t in_dim,
                               int64_t ldx, const float* Cs, const float* G, const float* W,
                               const float* b, int32_t num_classes, float* logits,

@@ -373,22 +373,11 @@ mck_status_t mck_features(mck_plan_t p, const float* x, int64_t n, int64_t in_di
                   "mck_features");
 }
 
-static int64_t num_partials(const mck_plan_s* p, int64_t n) {
-  const int T = 1 << (p->L - 5);
-  const int vpw = 32 / T;
-  const int spi = vpw >= 8 ? vpw : 8;
-  const int64_t tiles = (n + spi - 1) / spi;
-  const int64_t target = (int64_t)p->num_sms * 8;
-  int64_t wpe = (target + p->E - 1) / p->E;
-  wpe = wpe < 1 ? 1 : (wpe > tiles ? tiles : wpe);
-  return wpe * p->E;
-}
-
 static mck_status_t run_backward(mck_plan_s* p, BackwardArgs b, cudaStream_t s, const char* who) {
   const int64_t n = b.f.n;
   if (n == 0) return MCK_OK;
   const bool params = b.dCs || b.dG || b.phi_out;
-  const int64_t np = params ? num_partials(p, n) : 0;
+  const int64_t np = params ? backward_partials(p->L, n, p->E, p->num_sms) : 0;
   Scratch part(s);
   MCK_TRY(part.alloc(sizeof(float) * (size_t)np * 2 * p->d));
   return launched(launch_backward(b, (float*)part.ptr, np, s), who);
@@ -439,7 +428,8 @@ mck_status_t mck_fused_logits(mck_plan_t p, const float* x, int64_t n, int64_t i
   MCK_TRY(check_array(logits, 4 * n * C, p->device, "logits"));
   cudaStream_t s = (cudaStream_t)stream;
   Scratch part(s);
-  if (logits_need_scratch(p->L)) MCK_TRY(part.alloc(sizeof(float) * (size_t)n * p->E * C));
+  const int64_t nparts = logits_scratch_floats(p->L, n, p->E, C, p->num_sms);
+  if (nparts > 0) MCK_TRY(part.alloc(sizeof(float) * (size_t)nparts));
   return launched(launch_logits(feature_args(p, x, n, in_dim, ldx, Cs, G), W, b, C,
                                 (float*)part.ptr, logits, s),
                   "mck_fused_logits");

@@ -156,6 +156,16 @@ __device__ __forceinline__ float lds32(uint32_t addr) {
   asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
   return v;
 }
+// Named barriers (ids 1..15; id 0 is __syncthreads). `threads` counts every
+// thread that takes part, arriving or waiting, in whole warps. bar.sync waits;
+// bar.arrive only signals, and the memory accesses before it are visible to
+// the threads that waited on the same barrier.
+__device__ __forceinline__ void named_barrier(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int threads) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
 // Streaming (evict-first) 128-bit global store: the feature matrix is written
 // once and not re-read by the kernel, so it should not displace the tables.
 __device__ __forceinline__ void stg128_cs(float* p, float a, float b, float c, float d) {

@@ -446,49 +446,113 @@ __global__ void __launch_bounds__(128) k_feat_tiny(const Launch P) {
   }
 }
 
+// logits[n][c] = b[c] + sum_e part[n][e][c], expansions summed in order.
+__global__ void k_logits_reduce(const float* __restrict__ part, const float* __restrict__ b,
+                                int64_t n, int E, int C, float* __restrict__ logits) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * C) return;
+  const int64_t i = t / C;
+  const int c = (int)(t % C);
+  float s = 0.f;
+  for (int e = 0; e < E; ++e) s += part[(i * E + e) * C + c];
+  logits[t] = s + (b ? b[c] : 0.f);
+}
+
 // ---------------------------------------------------------------------------
-// Fused logits at d = 1024: a block of 8 warps owns a tile of 8 rows. For each
-// expansion every warp computes its row's 2048 features (the feature kernel's
-// sequence) into a shared 8 x 2048 tile; then the 256 threads contract the
-// tile with W: thread (class group cg, feature thread ft) owns classes
-// [cg*CPT, cg*CPT + CPT) and features ft, ft + TPG, ... for all 8 rows, so
-// each weight is loaded once per 8 rows. Partial sums stay in registers over
-// all expansions and are reduced once per tile in a fixed order.
+// Fused logits at d = 1024, warp-specialised. A block of 16 warps owns tiles
+// of 8 rows. Warps 0..7 produce: for each (tile, expansion e) warp w computes
+// the 2048 features of row w (the feature kernel's sequence) into its 8 KB
+// slice of one of two shared 8 x 2048 phi buffers; the slice is also the
+// warp's transpose buffer while the transforms run. Warps 8..15 consume: they
+// contract the buffer with W_e while the producers fill the other one. The
+// buffers change hands on named barriers (FULL: producers arrive, consumers
+// wait; EMPTY: the reverse). Consumer thread (class group cg, feature thread
+// ft) owns classes [cg*CPT, cg*CPT + CPT) and float4 columns ft, ft + TPG, ...
+// of all 8 rows, so each weight is loaded once per 8 rows, one column ahead of
+// its use; its 8 x CPT partial sums stay in registers for the whole tile and
+// are reduced once per tile in a fixed order.
 // ---------------------------------------------------------------------------
 constexpr int kTileRows = 8;
+constexpr int kTileWarps = 2 * kTileRows;
 
-template <int CPT>
-__global__ void __launch_bounds__(kTileRows * 32, 1) k_logits_tile(const Launch P,
-                                                                    const float* __restrict__ b,
-                                                                    float* __restrict__ logits) {
+// Chunks of expansions per tile: 1 while the tiles alone fill the SMs, else
+// as many as keep one block per SM busy (a batch of 512 rows has 64 tiles).
+int logits_echunks(int64_t n, int E, int num_sms) {
+  const int64_t tiles = (n + kTileRows - 1) / kTileRows;
+  if (tiles >= num_sms) return 1;
+  const int64_t c = num_sms / tiles;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(c, E));
+}
+constexpr int kTileThreads = kTileWarps * 32;
+constexpr int kConsumers = kTileRows * 32;
+constexpr int kBarFull = 1, kBarEmpty = 3, kBarReduce = 5;  // ids 1-2, 3-4, 5
+
+// One float4 column of CPT weight rows. W streams through once per tile: the
+// loads skip L1 so that the producers' tables and rows stay there.
+template <int CPT, int CG>
+__device__ __forceinline__ void load_w_col(const float* __restrict__ Wg, int64_t F, int C, int cg,
+                                           int f4, float4 (&w)[CPT]) {
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) {
+    w[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (cg * CPT + c < C) {
+      const float4* q = reinterpret_cast<const float4*>(Wg + c * F) + f4;
+      asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+          : "=f"(w[c].x), "=f"(w[c].y), "=f"(w[c].z), "=f"(w[c].w)
+          : "l"(q));
+    }
+  }
+}
+
+template <int CPT, int CG>
+__global__ void __launch_bounds__(kTileThreads, 1) k_logits_tile(const Launch P,
+                                                                 const float* __restrict__ b,
+                                                                 float* __restrict__ logits,
+                                                                 int echunks) {
   constexpr int L = 10;
   using Y = Lay<L>;
-  constexpr int d = Y::d, F2 = 2 * d;
+  constexpr int d = Y::d, F2 = 2 * d, F24 = F2 / 4;
+  constexpr int TPG = kConsumers / CG;  // consumer threads per class group
+  constexpr int ITER = F24 / TPG;       // float4 columns per consumer thread and expansion
+  static_assert(Y::SLOT <= F2 && F24 % TPG == 0 && TPG % 32 == 0, "tile shape");
+  static_assert(kTileRows * 12 == 3 * (d / 32), "8 producer warps x 12 lines cover permB, G and Cs");
   extern __shared__ float4 sm4[];
-  float* phis = reinterpret_cast<float*>(sm4);        // [kTileRows][F2]
-  float* bufs = phis + kTileRows * F2;                 // [kTileRows][SLOT]
-  float* red = bufs + kTileRows * Y::SLOT;             // [8 warps][kTileRows][CPT] reduction
+  float* phis = reinterpret_cast<float*>(sm4);  // [2][kTileRows][F2]
+  float* red = phis + 2 * kTileRows * F2;       // [8 consumer warps][kTileRows][CPT]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* buf = bufs + warp * Y::SLOT;
-  const uint32_t slot = smem_addr(buf);
   const int C = P.C, E = P.a.E;
-  const int CG = (C + CPT - 1) / CPT;                  // class groups (1 or 2)
-  const int TPG = (kTileRows * 32) / CG;               // threads per group
-  const int cg = threadIdx.x / TPG, ft = threadIdx.x % TPG;
   const int64_t F = 2ll * E * d;
+  // Work units: (tile, chunk of expansions); with echunks > 1 a unit writes
+  // its partial logits (no bias) for a later fixed-order sum over chunks.
   const int64_t tiles = (P.a.n + kTileRows - 1) / kTileRows;
-  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    float acc[kTileRows][CPT];
-#pragma unroll
-    for (int s = 0; s < kTileRows; ++s)
-#pragma unroll
-      for (int c = 0; c < CPT; ++c) acc[s][c] = 0.f;
-    const int64_t n = tile * kTileRows + warp;
-    const bool valid = n < P.a.n;
-    for (int e = 0; e < E; ++e) {
-      const int64_t off = (int64_t)e * d;
-      // ---- features of row n, expansion e -> phis[warp][.] ----
-      {
+  const int64_t units = tiles * echunks;
+  if (warp < kTileRows) {
+    // ------------------------------ producers ------------------------------
+    int64_t step = 0;
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+      const int64_t tile = u / echunks;
+      const int ch = (int)(u % echunks);
+      const int e0 = E * ch / echunks, e1 = E * (ch + 1) / echunks;
+      const int64_t n = tile * kTileRows + warp;
+      const bool valid = n < P.a.n;
+      for (int e = e0; e < e1; ++e, ++step) {
+        const int bsel = (int)(step & 1);
+        if (step >= 2) named_barrier(kBarEmpty + bsel, kTileThreads);
+        float* buf = phis + (bsel * kTileRows + warp) * F2;
+        const uint32_t slot = smem_addr(buf);
+        const int64_t off = (int64_t)e * d;
+        {  // the next step's tables (permB, G, Cs: 96 lines of 128 B) into L1, 12 per warp
+          const int64_t offn = (int64_t)(e + 1 < E ? e + 1 : 0) * d;
+          if (lane < 12) {
+            const int li = warp * 12 + lane;
+            const float* gsrc = P.a.GB ? P.a.GB : P.a.G;
+            const char* line =
+                li < 32   ? reinterpret_cast<const char*>(P.a.permB + offn) + li * 128
+                : li < 64 ? reinterpret_cast<const char*>(gsrc + offn) + (li - 32) * 128
+                          : reinterpret_cast<const char*>(P.a.Cs + offn) + (li - 64) * 128;
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(line));
+          }
+        }
         const uint32_t bmask = __ldg(P.a.maskA + (int64_t)e * Y::T + lane);
         uint32_t poff[16];
         float gt[32];
@@ -532,7 +596,7 @@ __global__ void __launch_bounds__(kTileRows * 32, 1) k_logits_tile(const Launch 
         __syncwarp();
         load_A<L>(buf, 0, lane, w);
         hreg<Y::maskA()>(w);
-        float* ph = phis + warp * F2;
+        __syncwarp();  // every lane holds its values: the slice takes the features now
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
           const int k0 = Y::kA(lane, 4 * m);
@@ -543,88 +607,126 @@ __global__ void __launch_bounds__(kTileRows * 32, 1) k_logits_tile(const Launch 
           for (int q = 0; q < 4; ++q) cos_sin(cs[q] * w[4 * m + q], c[q], s4[q]);
           // an invalid row contributes nothing
           if (!valid) c[0] = c[1] = c[2] = c[3] = s4[0] = s4[1] = s4[2] = s4[3] = 0.f;
-          *reinterpret_cast<float4*>(ph + k0) = make_float4(c[0], c[1], c[2], c[3]);
-          *reinterpret_cast<float4*>(ph + d + k0) = make_float4(s4[0], s4[1], s4[2], s4[3]);
+          *reinterpret_cast<float4*>(buf + k0) = make_float4(c[0], c[1], c[2], c[3]);
+          *reinterpret_cast<float4*>(buf + d + k0) = make_float4(s4[0], s4[1], s4[2], s4[3]);
         }
+        named_arrive(kBarFull + bsel, kTileThreads);
       }
-      __syncthreads();
-      // ---- contraction of the 8-row tile with W_e ----
-      const float* Wg = P.W + (int64_t)(cg * CPT) * F + 2ll * e * d;
-      for (int f = ft; f < F2; f += TPG) {
-        float p[kTileRows];
+    }
+    // Wait out the consumers' last two releases so every arrival is matched.
+    for (int64_t s = step < 2 ? 2 : step; s < step + 2; ++s)
+      named_barrier(kBarEmpty + (int)(s & 1), kTileThreads);
+    return;
+  }
+  // ------------------------------- consumers -------------------------------
+  const int ct = threadIdx.x - kConsumers, cw = ct >> 5;
+  const int cg = ct / TPG, ft = ct % TPG;
+  const float* Wc = P.W + (int64_t)(cg * CPT) * F;
+  // Up to 5 classes per thread the next column's weights are loaded one column
+  // ahead (2 x 5 float4 registers); with more, at their use, to avoid spills.
+  constexpr bool kAhead = CPT <= 5;
+  int64_t step = 0;
+  float4 wn[CPT];
+  if (kAhead && blockIdx.x < units) {
+    const int ch = (int)(blockIdx.x % echunks);
+    load_w_col<CPT, CG>(Wc + 2ll * (E * ch / echunks) * d, F, C, cg, ft, wn);
+  }
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int64_t tile = u / echunks;
+    const int ch = (int)(u % echunks);
+    const int e0 = E * ch / echunks, e1 = E * (ch + 1) / echunks;
+    float acc[kTileRows * CPT];
 #pragma unroll
-        for (int s = 0; s < kTileRows; ++s) p[s] = phis[s * F2 + f];
+    for (int i = 0; i < kTileRows * CPT; ++i) acc[i] = 0.f;
+    for (int e = e0; e < e1; ++e, ++step) {
+      const int bsel = (int)(step & 1);
+      const float4* ph4 = reinterpret_cast<const float4*>(phis + bsel * kTileRows * F2);
+      const float* Wg = Wc + 2ll * e * d;
+      named_barrier(kBarFull + bsel, kTileThreads);
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-          if (cg * CPT + c < C) {
-            const float wv = __ldg(Wg + c * F + f);
+      for (int it = 0; it < ITER; ++it) {
+        float4 wv[CPT];
+        if constexpr (kAhead) {
 #pragma unroll
-            for (int s = 0; s < kTileRows; ++s) acc[s][c] = fmaf(wv, p[s], acc[s][c]);
+          for (int c = 0; c < CPT; ++c) wv[c] = wn[c];
+          // the next column: this expansion's, else the next step's first
+          if (it + 1 < ITER) {
+            load_w_col<CPT, CG>(Wg, F, C, cg, ft + (it + 1) * TPG, wn);
+          } else {
+            int en = e + 1;
+            bool more = en < e1;
+            if (!more && u + gridDim.x < units) {
+              more = true;
+              en = E * (int)((u + gridDim.x) % echunks) / echunks;
+            }
+            if (more) load_w_col<CPT, CG>(Wc + 2ll * en * d, F, C, cg, ft, wn);
+          }
+        } else {
+          load_w_col<CPT, CG>(Wg, F, C, cg, ft + it * TPG, wv);
+        }
+        const int f4 = ft + it * TPG;
+#pragma unroll
+        for (int s = 0; s < kTileRows; ++s) {
+          const float4 p = ph4[s * F24 + f4];
+#pragma unroll
+          for (int c = 0; c < CPT; ++c) {
+            float t = acc[s * CPT + c];
+            t = fmaf(wv[c].x, p.x, t);
+            t = fmaf(wv[c].y, p.y, t);
+            t = fmaf(wv[c].z, p.z, t);
+            acc[s * CPT + c] = fmaf(wv[c].w, p.w, t);
           }
         }
       }
-      __syncthreads();
+      named_arrive(kBarEmpty + bsel, kTileThreads);
     }
     // ---- reduce over the TPG threads of each class group (fixed order) ----
 #pragma unroll
-    for (int s = 0; s < kTileRows; ++s)
+    for (int i = 0; i < kTileRows * CPT; ++i) {
+      float t = acc[i];
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) {
-        float t = acc[s][c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        acc[s][c] = t;
-      }
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      acc[i] = t;
+    }
     if (lane == 0) {
 #pragma unroll
-      for (int s = 0; s < kTileRows; ++s)
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) red[(warp * kTileRows + s) * CPT + c] = acc[s][c];
+      for (int i = 0; i < kTileRows * CPT; ++i) red[cw * kTileRows * CPT + i] = acc[i];
     }
-    __syncthreads();
-    const int wpg = TPG / 32;  // warps per class group
-    for (int o = threadIdx.x; o < kTileRows * C; o += blockDim.x) {
+    named_barrier(kBarReduce, kConsumers);
+    constexpr int wpg = TPG / 32;  // consumer warps per class group
+    for (int o = ct; o < kTileRows * C; o += kConsumers) {
       const int s = o / C, cls = o % C;
       const int g2 = cls / CPT, c = cls % CPT;
       float t = 0.f;
-      for (int q = 0; q < wpg; ++q) t += red[((g2 * wpg + q) * kTileRows + s) * CPT + c];
+      for (int q = 0; q < wpg; ++q) t += red[(g2 * wpg + q) * kTileRows * CPT + s * CPT + c];
       const int64_t row = tile * kTileRows + s;
-      if (row < P.a.n) logits[row * C + cls] = t + (b ? b[cls] : 0.f);
+      if (row < P.a.n) {
+        if (echunks == 1) logits[row * C + cls] = t + (b ? b[cls] : 0.f);
+        else P.part[(row * echunks + ch) * C + cls] = t;
+      }
     }
-    __syncthreads();
+    named_barrier(kBarReduce, kConsumers);  // red is free for the next tile
   }
 }
 
-template <int CPT>
+template <int CPT, int CG>
 cudaError_t run_logits_tile(const Launch& P, const float* b, float* logits, cudaStream_t s) {
   using Y = Lay<10>;
-  const size_t smem = sizeof(float) * (kTileRows * 2 * Y::d + kTileRows * Y::SLOT +
-                                       kTileRows * kTileRows * CPT);
-  cudaError_t err = cudaFuncSetAttribute(k_logits_tile<CPT>,
+  const size_t smem = sizeof(float) * (2 * kTileRows * 2 * Y::d + kTileRows * kTileRows * CPT);
+  cudaError_t err = cudaFuncSetAttribute(k_logits_tile<CPT, CG>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_logits_tile<CPT>, kTileRows * 32,
-                                                    smem) != cudaSuccess)
-    occ = 1;
-  occ = std::max(occ, 1);
-  const int64_t tiles = (P.a.n + kTileRows - 1) / kTileRows;
+  const int echunks = logits_echunks(P.a.n, P.a.E, P.a.num_sms);
+  const int64_t units = (P.a.n + kTileRows - 1) / kTileRows * echunks;
   const unsigned grid =
-      (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)P.a.num_sms * occ));
-  k_logits_tile<CPT><<<grid, kTileRows * 32, smem, s>>>(P, b, logits);
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)P.a.num_sms));
+  k_logits_tile<CPT, CG><<<grid, kTileThreads, smem, s>>>(P, b, logits, echunks);
+  err = cudaGetLastError();
+  if (err != cudaSuccess || echunks == 1) return err;
+  const int64_t total = P.a.n * P.C;
+  k_logits_reduce<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(P.part, b, P.a.n, echunks, P.C,
+                                                                  logits);
   return cudaGetLastError();
-}
-
-// logits[n][c] = b[c] + sum_e part[n][e][c], expansions summed in order.
-__global__ void k_logits_reduce(const float* __restrict__ part, const float* __restrict__ b,
-                                int64_t n, int E, int C, float* __restrict__ logits) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n * C) return;
-  const int64_t i = t / C;
-  const int c = (int)(t % C);
-  float s = 0.f;
-  for (int e = 0; e < E; ++e) s += part[(i * E + e) * C + c];
-  logits[t] = s + (b ? b[c] : 0.f);
 }
 
 template <class K>
@@ -701,7 +803,11 @@ cudaError_t launch_features(const FeatureArgs& a, float* phi, cudaStream_t s) {
   return dispatch<MODE_FEATURES>(P, s);
 }
 
-bool logits_need_scratch(int L) { return L != 10; }
+int64_t logits_scratch_floats(int L, int64_t n, int E, int C, int num_sms) {
+  if (L != 10) return n * E * C;
+  const int ec = logits_echunks(n, E, num_sms);
+  return ec > 1 ? n * ec * C : 0;
+}
 
 cudaError_t launch_logits(const FeatureArgs& a, const float* W, const float* b, int C,
                           float* part, float* logits, cudaStream_t s) {
@@ -711,16 +817,23 @@ cudaError_t launch_logits(const FeatureArgs& a, const float* W, const float* b, 
   P.part = part;
   P.C = C;
   if (a.L == 10) {  // tile kernel: logits written directly, no partials
-    const int cg = C <= 8 ? 1 : 2;
-    switch ((C + cg - 1) / cg) {
-      case 1: return run_logits_tile<1>(P, b, logits, s);
-      case 2: return run_logits_tile<2>(P, b, logits, s);
-      case 3: return run_logits_tile<3>(P, b, logits, s);
-      case 4: return run_logits_tile<4>(P, b, logits, s);
-      case 5: return run_logits_tile<5>(P, b, logits, s);
-      case 6: return run_logits_tile<6>(P, b, logits, s);
-      case 7: return run_logits_tile<7>(P, b, logits, s);
-      default: return run_logits_tile<8>(P, b, logits, s);
+    if (C <= 8) {
+      switch (C) {
+        case 1: return run_logits_tile<1, 1>(P, b, logits, s);
+        case 2: return run_logits_tile<2, 1>(P, b, logits, s);
+        case 3: return run_logits_tile<3, 1>(P, b, logits, s);
+        case 4: return run_logits_tile<4, 1>(P, b, logits, s);
+        case 5: return run_logits_tile<5, 1>(P, b, logits, s);
+        case 6: return run_logits_tile<6, 1>(P, b, logits, s);
+        case 7: return run_logits_tile<7, 1>(P, b, logits, s);
+        default: return run_logits_tile<8, 1>(P, b, logits, s);
+      }
+    }
+    switch ((C + 1) / 2) {
+      case 5: return run_logits_tile<5, 2>(P, b, logits, s);
+      case 6: return run_logits_tile<6, 2>(P, b, logits, s);
+      case 7: return run_logits_tile<7, 2>(P, b, logits, s);
+      default: return run_logits_tile<8, 2>(P, b, logits, s);
     }
   }
   cudaError_t err = dispatch<MODE_LOGITS>(P, s);

@@ -86,10 +86,6 @@ struct GArgs {
   bool vec_x;
 };
 
-__device__ __forceinline__ void named_barrier(int id, int threads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
-}
-
 __device__ __forceinline__ void apply_signs(float (&w)[32], uint32_t mask) {
 #pragma unroll
   for (int j = 0; j < 32; ++j)

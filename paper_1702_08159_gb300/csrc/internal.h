@@ -70,7 +70,8 @@ struct FeatureArgs {
 cudaError_t launch_features(const FeatureArgs& a, float* phi, cudaStream_t s);
 // Partial logits per (sample, expansion): part is n x E x C; then logits = sum_e part + b.
 // At d = 1024 the tile kernel writes logits directly and `part` is unused.
-bool logits_need_scratch(int L);
+// Floats of partial logits launch_logits needs in `part` (0: none).
+int64_t logits_scratch_floats(int L, int64_t n, int E, int C, int num_sms);
 cudaError_t launch_logits(const FeatureArgs& a, const float* W, const float* b, int C,
                           float* part, float* logits, cudaStream_t s);
 
@@ -89,7 +90,9 @@ struct BackwardArgs {
   float* dCs;
   float* dG;
 };
-// partials: num_partials x 2 x d floats, num_partials = E x (warps per expansion).
+// Partial rows of dCs/dG sums the adjoint writes: E x (blocks per expansion).
+int64_t backward_partials(int L, int64_t n, int E, int num_sms);
+// partials: num_partials x 2 x d floats, num_partials = backward_partials(...).
 cudaError_t launch_backward(const BackwardArgs& a, float* partials, int64_t num_partials,
                             cudaStream_t s);
 cudaError_t launch_logit_weight_grads(const float* dlogits, const float* phi, int64_t n, int C,

@@ -22,6 +22,8 @@
 // All sums run in a fixed order, so results are bit-reproducible.
 #include <cuda_runtime.h>
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -30,7 +32,11 @@
 namespace mck {
 namespace {
 
-constexpr int kBW = 4;  // warps per block
+namespace cg = cooperative_groups;
+
+constexpr int kBW = 1;         // warps per block
+constexpr int kBwdMinBlocks = 12;  // resident single-warp blocks per SM the registers must allow
+constexpr int kBwdInputMinBlocks = 8;  // k_bwd_input keeps dx in registers as well
 constexpr int CMAX = MCK_MAX_CLASSES;
 
 // ---------------------------------------------------------------------------
@@ -83,8 +89,9 @@ struct BShape {
 struct BwdLaunch {
   BackwardArgs b;
   bool vec_x;
-  float* partials;  // [warps][2][d]
-  int wpe;          // warps per expansion (k_bwd_params)
+  float* partials;  // [E][bpe][2][d]
+  int bpe;          // blocks per expansion (k_bwd_params)
+  bool w_smem;      // k_bwd_params stages W_e in shared memory
 };
 
 __device__ __forceinline__ void apply_signs(float (&w)[32], uint32_t mask) {
@@ -93,56 +100,109 @@ __device__ __forceinline__ void apply_signs(float (&w)[32], uint32_t mask) {
     w[j] = __int_as_float(__float_as_int(w[j]) ^ ((mask << (31 - j)) & 0x80000000u));
 }
 
-template <int L>
-__device__ __forceinline__ uint32_t load_bmask_A(const uint32_t* __restrict__ Bw, int lam) {
-  uint32_t mask = 0;
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const int k0 = Lay<L>::kA(lam, 4 * m);
-    mask |= ((__ldg(Bw + (k0 >> 5)) >> (k0 & 31)) & 0xFu) << (4 * m);
-  }
-  return mask;
+// Per-lane arrays in shared memory hold a lane's 32 values as 8 float4s,
+// float4 m of lane l at index m * 32 + l: private to the lane, and a warp's
+// 128-bit accesses are conflict free.
+__device__ __forceinline__ float4& lane4(float* a, int m, int lane) {
+  return reinterpret_cast<float4*>(a)[m * 32 + lane];
 }
 
-// Per-warp shared state of the backward kernels. Arrays indexed [j][lane]
-// are private to a lane (bank-conflict free).
-template <int L>
+// Per-warp shared state of the backward kernels. Only k_bwd_params keeps the
+// sample's v and the running sums.
+template <int L, bool PARAMS>
 struct BwdSmem {
-  float buf[BShape<L>::VPW * Lay<L>::SLOT];
-  float gl[32 * 32];   // G in layout B
-  float csl[32 * 32];  // Cs in layout A
-  float vl[32 * 32];   // v = Pi u of the current sample, layout B
-  float dcs[32 * 32];  // running sum of h dz, layout A
-  float dg[32 * 32];   // running sum of v dw, layout B
+  alignas(16) float buf[BShape<L>::VPW * Lay<L>::SLOT];
+  alignas(16) float vl[PARAMS ? 32 * 32 : 4];   // v = Pi u of the current sample, layout B
+  alignas(16) float dcs[PARAMS ? 32 * 32 : 4];  // running sum of h dz, layout A
+  alignas(16) float dg[PARAMS ? 32 * 32 : 4];   // running sum of v dw, layout B
+  alignas(16) float dl[BShape<L>::VPW * CMAX];  // dlogits of the warp's current samples (fused)
 };
 
+// Where bwd_core finds G_e, Cs_e and W_e: per-lane copies in shared memory
+// ([j][lane], shared by the block's warps, which all work on expansion e) and
+// W_e's 2d columns per class (stride 2d), or else global memory.
+struct BwdTabs {
+  float* gl;   // per-lane G in layout B, or null: read G from global
+  float* csl;  // per-lane Cs in layout A, or null: read Cs from global
+  uint32_t ws;       // shared address of W_e (C x 2d), or 0: read W from global
+};
+
+// Tables of expansion e held in registers for the warp's samples: B as a bit
+// mask over layout A, Pi as byte offsets into the vector slot (packed two per
+// register; the gather reads and the adjoint's scatter writes them).
 template <int L>
-__device__ __forceinline__ void load_tables(const FeatureArgs& a, int e, int g, int lam, int lane,
-                                            uint32_t buf_addr, BwdSmem<L>& S, uint32_t& bmask,
-                                            uint32_t (&paddr)[32]) {
+__device__ __forceinline__ void load_tables(const FeatureArgs& a, int e, int lam, uint32_t& bmask,
+                                            uint32_t (&poff)[16]) {
   using Y = Lay<L>;
-  constexpr int d = Y::d;
-  const int64_t off = (int64_t)e * d;
-  bmask = load_bmask_A<L>(a.B_bits + (int64_t)e * (d / 32), lam);
+  const int64_t off = (int64_t)e * Y::d;
+  bmask = __ldg(a.maskA + (int64_t)e * Y::T + lam);
+  const uint4* pb = reinterpret_cast<const uint4*>(a.permB + off) + lam;
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    const int k = Y::kB(lam, j);
-    S.gl[j * 32 + lane] = __ldg(a.G + off + k);
-    paddr[j] = buf_addr + 4u * (uint32_t)spos<L>(g, (int)__ldg(a.perm + off + k));
-    S.csl[j * 32 + lane] = __ldg(a.Cs + off + Y::kA(lam, j));
+  for (int m = 0; m < 8; ++m) {
+    const uint4 v = __ldg(pb + m * Y::T);
+    poff[2 * m] = v.x | (v.y << 16);
+    poff[2 * m + 1] = v.z | (v.w << 16);
+  }
+}
+
+__device__ __forceinline__ uint32_t poff_of(const uint32_t (&poff)[16], int j) {
+  return (j & 1) ? (poff[j >> 1] >> 16) : (poff[j >> 1] & 0xffffu);
+}
+
+__device__ __forceinline__ float4 lds128(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(addr));
+  return v;
+}
+
+// G_e in layout B: from the block's shared copy, the plan's lane-ordered
+// copy, or an overriding G.
+template <int L>
+__device__ __forceinline__ void load_G_B(const FeatureArgs& a, const BwdTabs& tb, int e, int lam,
+                                         float (&gt)[32]) {
+  using Y = Lay<L>;
+  const int lane = threadIdx.x & 31;
+  const int64_t off = (int64_t)e * Y::d;
+  if (tb.gl) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const float4 v = lane4(tb.gl, m, lane);
+      gt[4 * m] = v.x;
+      gt[4 * m + 1] = v.y;
+      gt[4 * m + 2] = v.z;
+      gt[4 * m + 3] = v.w;
+    }
+  } else if (a.GB) {
+    const float4* gb = reinterpret_cast<const float4*>(a.GB + off) + lam;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const float4 v = __ldg(gb + m * Y::T);
+      gt[4 * m] = v.x;
+      gt[4 * m + 1] = v.y;
+      gt[4 * m + 2] = v.z;
+      gt[4 * m + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) gt[j] = __ldg(a.G + off + Y::kB(lam, j));
   }
 }
 
 // One sample of one expansion: forward recompute and backward. On return w
 // holds B du0 (layout A), the sample's contribution to dx-hat.
 template <int L, bool FUSED, bool PARAMS>
-__device__ __forceinline__ void bwd_core(const BwdLaunch& P, int64_t n, int e, bool valid, int g,
-                                         int lam, int lane, BwdSmem<L>& S, uint32_t bmask,
-                                         const uint32_t (&paddr)[32], float (&w)[32]) {
+__device__ __forceinline__ void bwd_core(const BwdLaunch& P, const BwdTabs& tb, int64_t n, int e,
+                                         bool valid, int g, int lam, BwdSmem<L, PARAMS>& S,
+                                         uint32_t slot, uint32_t bmask,
+                                         const uint32_t (&poff)[16], float (&w)[32]) {
   using Y = Lay<L>;
   constexpr int d = Y::d;
   const FeatureArgs& a = P.b.f;
   const int64_t F = 2ll * a.E * d;
+  const int64_t off = (int64_t)e * d;
+  const int lane = threadIdx.x & 31;
   float* buf = S.buf;
   // ---- forward: u = H B x-hat, v = Pi u, h = H G v ----
   {
@@ -177,14 +237,18 @@ __device__ __forceinline__ void bwd_core(const BwdLaunch& P, int64_t n, int e, b
   hreg<Y::maskB()>(w);
   store_B<L>(buf, g, lam, w);
   __syncwarp();
-  float gt[32];
+  {
+    float gt[32];
+    load_G_B<L>(a, tb, e, lam, gt);
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    w[j] = lds32(paddr[j]);
-    if constexpr (PARAMS) S.vl[j * 32 + lane] = w[j];
-    gt[j] = S.gl[j * 32 + lane];
+    for (int j = 0; j < 32; ++j) w[j] = lds32(slot + poff_of(poff, j));
+    if constexpr (PARAMS) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m)
+        lane4(S.vl, m, lane) = make_float4(w[4 * m], w[4 * m + 1], w[4 * m + 2], w[4 * m + 3]);
+    }
+    hreg_scaled<Y::maskB()>(w, gt);
   }
-  hreg_scaled<Y::maskB()>(w, gt);
   __syncwarp();
   if constexpr (L > 5) {
     store_B<L>(buf, g, lam, w);
@@ -193,49 +257,80 @@ __device__ __forceinline__ void bwd_core(const BwdLaunch& P, int64_t n, int e, b
   }
   hreg<Y::maskA()>(w);  // w = h, layout A
   // ---- dz from the upstream gradient ----
-  float dl[CMAX];
+  // dphi for the lane's elements: from memory, or formed as W_e^T dlogits
+  // class by class (64 accumulators, one dlogits value per class).
+  float dc[32], ds[32];
   if constexpr (FUSED) {
+    for (int c = lam; c < P.b.C; c += Y::T)  // dlogits of sample n, shared by its group's lanes
+      S.dl[g * CMAX + c] = valid ? __ldg(P.b.dlogits + n * P.b.C + c) : 0.f;
+    __syncwarp();
 #pragma unroll
-    for (int c = 0; c < CMAX; ++c)
-      dl[c] = (valid && c < P.b.C) ? __ldg(P.b.dlogits + n * P.b.C + c) : 0.f;
+    for (int j = 0; j < 32; ++j) dc[j] = ds[j] = 0.f;
+    const float* wr = P.b.W + 2ll * e * d;
+#pragma unroll 1
+    for (int c = 0; c < P.b.C; ++c) {
+      const float dlc = S.dl[g * CMAX + c];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int k0 = Y::kA(lam, 4 * m);
+        float4 wc, ws;
+        if (tb.ws) {
+          const uint32_t wa = tb.ws + 4u * (uint32_t)(c * 2 * d + k0);
+          wc = lds128(wa);
+          ws = lds128(wa + 4u * d);
+        } else {
+          wc = __ldg(reinterpret_cast<const float4*>(wr + c * F + k0));
+          ws = __ldg(reinterpret_cast<const float4*>(wr + c * F + d + k0));
+        }
+        dc[4 * m] = fmaf(dlc, wc.x, dc[4 * m]);
+        dc[4 * m + 1] = fmaf(dlc, wc.y, dc[4 * m + 1]);
+        dc[4 * m + 2] = fmaf(dlc, wc.z, dc[4 * m + 2]);
+        dc[4 * m + 3] = fmaf(dlc, wc.w, dc[4 * m + 3]);
+        ds[4 * m] = fmaf(dlc, ws.x, ds[4 * m]);
+        ds[4 * m + 1] = fmaf(dlc, ws.y, ds[4 * m + 1]);
+        ds[4 * m + 2] = fmaf(dlc, ws.z, ds[4 * m + 2]);
+        ds[4 * m + 3] = fmaf(dlc, ws.w, ds[4 * m + 3]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int k0 = Y::kA(lam, 4 * m);
+      float4 vc = make_float4(0.f, 0.f, 0.f, 0.f), vs = vc;
+      if (valid) {
+        const float* gr = P.b.dphi + n * F + 2ll * e * d + k0;
+        vc = __ldg(reinterpret_cast<const float4*>(gr));
+        vs = __ldg(reinterpret_cast<const float4*>(gr + d));
+      }
+      dc[4 * m] = vc.x; dc[4 * m + 1] = vc.y; dc[4 * m + 2] = vc.z; dc[4 * m + 3] = vc.w;
+      ds[4 * m] = vs.x; ds[4 * m + 1] = vs.y; ds[4 * m + 2] = vs.z; ds[4 * m + 3] = vs.w;
+    }
   }
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const int k0 = Y::kA(lam, 4 * m);
-    float dc[4] = {0.f, 0.f, 0.f, 0.f}, ds[4] = {0.f, 0.f, 0.f, 0.f};
-    if constexpr (FUSED) {
-      const float* wr = P.b.W + 2ll * e * d + k0;
-#pragma unroll
-      for (int c = 0; c < CMAX; ++c) {
-        if (c < P.b.C) {
-          const float4 wc = __ldg(reinterpret_cast<const float4*>(wr + c * F));
-          const float4 ws = __ldg(reinterpret_cast<const float4*>(wr + c * F + d));
-          dc[0] = fmaf(dl[c], wc.x, dc[0]);
-          dc[1] = fmaf(dl[c], wc.y, dc[1]);
-          dc[2] = fmaf(dl[c], wc.z, dc[2]);
-          dc[3] = fmaf(dl[c], wc.w, dc[3]);
-          ds[0] = fmaf(dl[c], ws.x, ds[0]);
-          ds[1] = fmaf(dl[c], ws.y, ds[1]);
-          ds[2] = fmaf(dl[c], ws.z, ds[2]);
-          ds[3] = fmaf(dl[c], ws.w, ds[3]);
-        }
-      }
-    } else if (valid) {
-      const float* gr = P.b.dphi + n * F + 2ll * e * d + k0;
-      const float4 vc = __ldg(reinterpret_cast<const float4*>(gr));
-      const float4 vs = __ldg(reinterpret_cast<const float4*>(gr + d));
-      dc[0] = vc.x; dc[1] = vc.y; dc[2] = vc.z; dc[3] = vc.w;
-      ds[0] = vs.x; ds[1] = vs.y; ds[2] = vs.z; ds[3] = vs.w;
+    float csq[4];
+    if (tb.csl) {
+      const float4 c4 = lane4(tb.csl, m, lane);
+      csq[0] = c4.x; csq[1] = c4.y; csq[2] = c4.z; csq[3] = c4.w;
+    } else {
+      const float4 c4 = __ldg(reinterpret_cast<const float4*>(a.Cs + off + k0));
+      csq[0] = c4.x; csq[1] = c4.y; csq[2] = c4.z; csq[3] = c4.w;
     }
-    float cz[4], sz[4];
+    float cz[4], sz[4], hz[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = 4 * m + q;
-      const float csj = S.csl[j * 32 + lane];
-      cos_sin(csj * w[j], cz[q], sz[q]);
-      const float dz = fmaf(-sz[q], dc[q], cz[q] * ds[q]);
-      if constexpr (PARAMS) S.dcs[j * 32 + lane] = fmaf(w[j], dz, S.dcs[j * 32 + lane]);
-      w[j] = csj * dz;  // dh
+      cos_sin(csq[q] * w[j], cz[q], sz[q]);
+      const float dz = fmaf(-sz[q], dc[j], cz[q] * ds[j]);
+      hz[q] = w[j] * dz;
+      w[j] = csq[q] * dz;  // dh
+    }
+    if constexpr (PARAMS) {
+      float4& acc = lane4(S.dcs, m, lane);
+      float4 t = acc;
+      t.x += hz[0]; t.y += hz[1]; t.z += hz[2]; t.w += hz[3];
+      acc = t;
     }
     if constexpr (FUSED && PARAMS) {
       if (valid && P.b.phi_out) {
@@ -254,14 +349,28 @@ __device__ __forceinline__ void bwd_core(const BwdLaunch& P, int64_t n, int e, b
   }
   hreg<Y::maskB()>(w);
   // ---- dG, dv = G dw, scatter du[pi(k)] = dv[k] ----
+  {
+    float gt[32];
+    load_G_B<L>(a, tb, e, lam, gt);
+    if constexpr (PARAMS) {
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    if constexpr (PARAMS) S.dg[j * 32 + lane] = fmaf(S.vl[j * 32 + lane], w[j], S.dg[j * 32 + lane]);
-    w[j] *= S.gl[j * 32 + lane];
+      for (int m = 0; m < 8; ++m) {
+        const float4 v = lane4(S.vl, m, lane);
+        float4& acc = lane4(S.dg, m, lane);
+        float4 t = acc;
+        t.x = fmaf(v.x, w[4 * m], t.x);
+        t.y = fmaf(v.y, w[4 * m + 1], t.y);
+        t.z = fmaf(v.z, w[4 * m + 2], t.z);
+        t.w = fmaf(v.w, w[4 * m + 3], t.w);
+        acc = t;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) w[j] *= gt[j];
   }
   __syncwarp();
 #pragma unroll
-  for (int j = 0; j < 32; ++j) sts32(paddr[j], w[j]);
+  for (int j = 0; j < 32; ++j) sts32(slot + poff_of(poff, j), w[j]);
   __syncwarp();
   load_B<L>(buf, g, lam, w);
   // ---- du0 = H du ----
@@ -276,49 +385,101 @@ __device__ __forceinline__ void bwd_core(const BwdLaunch& P, int64_t n, int e, b
   __syncwarp();
 }
 
+// dCs and dG partial sums. Block (e, sb) of kBP warps works on expansion e:
+// it stages G_e and Cs_e per lane (and W_e, when it fits) in shared memory;
+// warp q takes sample units (groups of VPW samples) [U q / W, U (q+1) / W) of
+// the W = bpe * kBP warps of e; at the end the warps' sums are added in warp
+// order and the block writes one partial row (E x bpe rows in all).
+constexpr int kBP = 8;  // warps per block of k_bwd_params
+
+template <int L>
+struct BwdBlockSmem {
+  alignas(16) float gl[32 * 32];
+  alignas(16) float csl[32 * 32];
+  BwdSmem<L, true> warp[kBP];
+  // followed by W_e (C x 2d floats) when staged
+};
+
 template <int L, bool FUSED>
-__global__ void __launch_bounds__(kBW * 32) k_bwd_params(const BwdLaunch P, int64_t nwarps) {
+__global__ void __launch_bounds__(kBP * 32, 1) k_bwd_params(const BwdLaunch P) {
   using Y = Lay<L>;
   using BS = BShape<L>;
   constexpr int d = Y::d;
   extern __shared__ float4 sm4[];
+  BwdBlockSmem<L>& B = *reinterpret_cast<BwdBlockSmem<L>*>(sm4);
+  float* Wsm = reinterpret_cast<float*>(&B + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  BwdSmem<L>& S = reinterpret_cast<BwdSmem<L>*>(sm4)[warp];
-  const int64_t wid = (int64_t)blockIdx.x * kBW + warp;
-  if (wid >= nwarps) return;
+  BwdSmem<L, true>& S = B.warp[warp];
   const int g = lane / Y::T, lam = lane % Y::T;
-  const uint32_t buf_addr = smem_addr(S.buf);
+  const uint32_t slot = smem_addr(S.buf) + 4u * (uint32_t)(g * Y::SLOT);
   const FeatureArgs& a = P.b.f;
-  const int e = (int)(wid / P.wpe), sub = (int)(wid % P.wpe);
-  const int64_t tiles = (a.n + BS::SPI - 1) / BS::SPI;
-  const int64_t t0 = tiles * sub / P.wpe, t1 = tiles * (sub + 1) / P.wpe;
-  uint32_t bmask;
-  uint32_t paddr[32];
-  load_tables<L>(a, e, g, lam, lane, buf_addr, S, bmask, paddr);
+  const int e = (int)(blockIdx.x / P.bpe), sb = (int)(blockIdx.x % P.bpe);
+  const int64_t off = (int64_t)e * d;
+  // ---- stage the expansion's tables ----
+  if (warp == 0) {
+    float gt[32];
+    const BwdTabs none{nullptr, nullptr, 0u};  // read G from global
+    load_G_B<L>(a, none, e, lam, gt);
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    S.dcs[j * 32 + lane] = 0.f;
-    S.dg[j * 32 + lane] = 0.f;
-  }
-  for (int64_t t = t0; t < t1; ++t) {
-    for (int r = 0; r < BS::R; ++r) {
-      const int64_t n = t * BS::SPI + r * BS::VPW + g;
-      const bool valid = n < a.n;
-      float w[32];
-      // An invalid sample contributes exactly zero: x-hat = 0 gives h = 0,
-      // and its upstream gradient is read as 0 (dphi) or dlogits = 0.
-      bwd_core<L, FUSED, true>(P, n, e, valid, g, lam, lane, S, bmask, paddr, w);
+    for (int m = 0; m < 8; ++m) {
+      lane4(B.gl, m, lane) = make_float4(gt[4 * m], gt[4 * m + 1], gt[4 * m + 2], gt[4 * m + 3]);
+      lane4(B.csl, m, lane) =
+          __ldg(reinterpret_cast<const float4*>(a.Cs + off + Y::kA(lam, 4 * m)));
     }
   }
-  // Sum the warp's sample groups (lanes with equal lam) and write the row.
-  float* pr = P.partials + wid * 2 * d;
+  if (FUSED && P.w_smem) {
+    const int64_t F = 2ll * a.E * d;
+    const int per_class4 = 2 * d / 4;
+    for (int i = threadIdx.x; i < P.b.C * per_class4; i += blockDim.x) {
+      const int c = i / per_class4, f4 = i % per_class4;
+      reinterpret_cast<float4*>(Wsm)[i] =
+          __ldg(reinterpret_cast<const float4*>(P.b.W + c * F + 2ll * e * d) + f4);
+    }
+  }
+  const BwdTabs tb{B.gl, B.csl, (FUSED && P.w_smem) ? smem_addr(Wsm) : 0u};
+  uint32_t bmask;
+  uint32_t poff[16];
+  load_tables<L>(a, e, lam, bmask, poff);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    lane4(S.dcs, m, lane) = make_float4(0.f, 0.f, 0.f, 0.f);
+    lane4(S.dg, m, lane) = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __syncthreads();
+  const int64_t units = (a.n + BS::VPW - 1) / BS::VPW;
+  const int64_t nw = (int64_t)P.bpe * kBP, q = (int64_t)sb * kBP + warp;
+  const int64_t u0 = units * q / nw, u1 = units * (q + 1) / nw;
+  for (int64_t u = u0; u < u1; ++u) {
+    const int64_t n = u * BS::VPW + g;
+    const bool valid = n < a.n;
+    float w[32];
+    // An invalid sample contributes exactly zero: x-hat = 0 gives h = 0,
+    // and its upstream gradient is read as 0 (dphi) or dlogits = 0.
+    bwd_core<L, FUSED, true>(P, tb, n, e, valid, g, lam, S, slot, bmask, poff, w);
+  }
+  // Sum the warp's sample groups (lanes with equal lam) into lanes of group 0,
+  // then the block's warps in order, and write the block's row.
+  // (element j of a lane sits at word (j / 4 * 32 + lane) * 4 + j % 4)
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
-    float s1 = S.dcs[j * 32 + lane], s2 = S.dg[j * 32 + lane];
+    const int at = ((j >> 2) * 32 + lane) * 4 + (j & 3);
+    float s1 = S.dcs[at], s2 = S.dg[at];
 #pragma unroll
     for (int o = Y::T; o < 32; o <<= 1) {
       s1 += __shfl_xor_sync(0xffffffffu, s1, o);
       s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    S.dcs[at] = s1;
+    S.dg[at] = s2;
+  }
+  __syncthreads();
+  float* pr = P.partials + ((int64_t)e * P.bpe + sb) * 2 * d;
+  for (int j = warp; j < 32; j += kBP) {
+    const int at = ((j >> 2) * 32 + lane) * 4 + (j & 3);
+    float s1 = 0.f, s2 = 0.f;
+    for (int w2 = 0; w2 < kBP; ++w2) {
+      s1 += B.warp[w2].dcs[at];
+      s2 += B.warp[w2].dg[at];
     }
     if (g == 0) {
       pr[Y::kA(lam, j)] = s1;
@@ -328,14 +489,14 @@ __global__ void __launch_bounds__(kBW * 32) k_bwd_params(const BwdLaunch P, int6
 }
 
 template <int L, bool FUSED>
-__global__ void __launch_bounds__(kBW * 32) k_bwd_input(const BwdLaunch P) {
+__global__ void __launch_bounds__(kBW * 32, kBwdInputMinBlocks) k_bwd_input(const BwdLaunch P) {
   using Y = Lay<L>;
   using BS = BShape<L>;
   extern __shared__ float4 sm4[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  BwdSmem<L>& S = reinterpret_cast<BwdSmem<L>*>(sm4)[warp];
+  BwdSmem<L, false>& S = reinterpret_cast<BwdSmem<L, false>*>(sm4)[warp];
   const int g = lane / Y::T, lam = lane % Y::T;
-  const uint32_t buf_addr = smem_addr(S.buf);
+  const uint32_t slot = smem_addr(S.buf) + 4u * (uint32_t)(g * Y::SLOT);
   const FeatureArgs& a = P.b.f;
   const int64_t steps = (a.n + BS::VPW - 1) / BS::VPW;
   for (int64_t st = (int64_t)blockIdx.x * kBW + warp; st < steps;
@@ -347,12 +508,11 @@ __global__ void __launch_bounds__(kBW * 32) k_bwd_input(const BwdLaunch P) {
     for (int j = 0; j < 32; ++j) dx[j] = 0.f;
     for (int e = 0; e < a.E; ++e) {
       uint32_t bmask;
-      uint32_t paddr[32];
-      __syncwarp();
-      load_tables<L>(a, e, g, lam, lane, buf_addr, S, bmask, paddr);
-      __syncwarp();
+      uint32_t poff[16];
+      load_tables<L>(a, e, lam, bmask, poff);
       float w[32];
-      bwd_core<L, FUSED, false>(P, n, e, valid, g, lam, lane, S, bmask, paddr, w);
+      const BwdTabs tb{nullptr, nullptr, 0u};
+      bwd_core<L, FUSED, false>(P, tb, n, e, valid, g, lam, S, slot, bmask, poff, w);
 #pragma unroll
       for (int j = 0; j < 32; ++j) dx[j] += w[j];
     }
@@ -367,96 +527,234 @@ __global__ void __launch_bounds__(kBW * 32) k_bwd_input(const BwdLaunch P) {
   }
 }
 
-// dCs[e][k] = sum over the expansion's warps of row 0; dG likewise row 1.
-__global__ void k_reduce_params(const float* __restrict__ partials, int64_t d, int E, int wpe,
-                                float* __restrict__ dCs, float* __restrict__ dG) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= d * E) return;
-  const int64_t e = t / d, k = t % d;
-  float s1 = 0.f, s2 = 0.f;
-  for (int q = 0; q < wpe; ++q) {
-    const float* pr = partials + ((e * wpe + q) * 2) * d;
-    s1 += pr[k];
-    s2 += pr[d + k];
+// dCs[e][k] = sum over the expansion's partial rows of row 0; dG likewise row 1.
+// A block owns 64 consecutive k of one expansion: thread (qg, c4) adds the
+// partial rows q = qg, qg + 16, ... of float4 column c4 in order, and the 16
+// groups are then added in order through shared memory.
+constexpr int kRpCols = 16, kRpGroups = 16;  // float4 columns x row groups per block
+
+__global__ void __launch_bounds__(kRpCols * kRpGroups) k_reduce_params(
+    const float* __restrict__ partials, int64_t d, int E, int rpe, float* __restrict__ dCs,
+    float* __restrict__ dG) {
+  __shared__ float4 red[2][kRpGroups][kRpCols];
+  const int c4 = threadIdx.x % kRpCols, qg = threadIdx.x / kRpCols;
+  const int cols = d / 4 < kRpCols ? (int)(d / 4) : kRpCols;  // d = 32 has 8 float4 columns
+  const int64_t blocks_per_e = d / (4 * cols);
+  const int64_t e = blockIdx.x / blocks_per_e;
+  const int64_t k = (blockIdx.x % blocks_per_e) * 4 * cols + 4 * c4;
+  const bool on = c4 < cols;
+  const float4* base = reinterpret_cast<const float4*>(partials + e * rpe * 2 * d + k);
+  const int64_t stride = 2 * d / 4;  // float4s between consecutive partial rows
+  float4 s1 = make_float4(0.f, 0.f, 0.f, 0.f), s2 = s1;
+  for (int q = qg; on && q < rpe; q += kRpGroups) {
+    const float4 a = __ldg(base + q * stride), b = __ldg(base + q * stride + d / 4);
+    s1.x += a.x; s1.y += a.y; s1.z += a.z; s1.w += a.w;
+    s2.x += b.x; s2.y += b.y; s2.z += b.z; s2.w += b.w;
   }
-  if (dCs) dCs[t] = s1;
-  if (dG) dG[t] = s2;
+  red[0][qg][c4] = s1;
+  red[1][qg][c4] = s2;
+  __syncthreads();
+  if (qg < 2 && on) {  // group 0 finishes dCs, group 1 dG
+    float4 t = red[qg][0][c4];
+    for (int q = 1; q < kRpGroups; ++q) {
+      const float4 v = red[qg][q][c4];
+      t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w;
+    }
+    float* o = qg == 0 ? dCs : dG;  // may be only 4-byte aligned
+    if (o) {
+      o += e * d + k;
+      o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    }
+  }
 }
 
-// dW[c][f] = sum_n dlogits[n][c] phi[n][f]. A block owns 32 consecutive
-// columns; its 8 warps take the rows n = w, w + 8, ... (one column per lane,
-// coalesced 128-byte row segments) and the 8 partial sums are added in warp
-// order through shared memory, so the result does not depend on scheduling.
+// dW[c][f] = sum_n dlogits[n][c] phi[n][f]. A block owns 128 consecutive
+// columns (a float4 per lane) and one of RS contiguous row ranges; the RS
+// blocks of a column range form a thread-block cluster. In a block the 8
+// warps take the rows r = w, w + 8, ... of its range, eight rows' loads in
+// flight per warp, with dlogits staged in shared memory a chunk of rows at a
+// time (rows padded to a multiple of 4 classes for 128-bit reads). Per class,
+// each block adds its 8 warp sums in warp order, and the cluster's rank 0
+// adds the RS block sums in rank order through distributed shared memory:
+// the result does not depend on scheduling.
 constexpr int kWgRowGroups = 8;
+constexpr int kWgChunk = 256;  // rows of dlogits staged per pass
+constexpr int kWgUnroll = 8;   // rows in flight per warp
 
+template <int C>
 __global__ void __launch_bounds__(32 * kWgRowGroups) k_weight_grads(const float* __restrict__ dl,
                                                                    const float* __restrict__ phi,
-                                                                   int64_t n, int C, int64_t F,
+                                                                   int64_t n, int64_t F,
                                                                    float* __restrict__ dW) {
-  __shared__ float part[kWgRowGroups][CMAX][32];
+  constexpr int C4 = (C + 3) / 4 * 4;  // padded row of dlogits in shared memory
+  __shared__ float4 dls4[kWgChunk * C4 / 4];
+  __shared__ float4 part[kWgRowGroups][32];
+  __shared__ float4 bsum[C][32];
+  float* dls = reinterpret_cast<float*>(dls4);
+  cg::cluster_group cluster = cg::this_cluster();
+  const int RS = (int)gridDim.y, ry = (int)blockIdx.y;  // cluster = the RS blocks of a column
   const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;
-  const int64_t f = (int64_t)blockIdx.x * 32 + lane;
-  float acc[CMAX];
+  const int64_t f = ((int64_t)blockIdx.x * 32 + lane) * 4;  // F is a multiple of 4
+  const bool active = f < F;
+  const int64_t rbeg = n * ry / RS, rend = n * (ry + 1) / RS;
+  float4 acc[C];
 #pragma unroll
-  for (int c = 0; c < CMAX; ++c) acc[c] = 0.f;
-  if (f < F) {
-    for (int64_t i = rg; i < n; i += kWgRowGroups) {
-      const float p = phi[i * F + f];
+  for (int c = 0; c < C; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto fma_row = [&](const float4& p, const float* dr) {
 #pragma unroll
-      for (int c = 0; c < CMAX; ++c)
-        if (c < C) acc[c] = fmaf(__ldg(dl + i * C + c), p, acc[c]);
-    }
-  }
+    for (int c4 = 0; c4 < C4 / 4; ++c4) {
+      const float4 g4 = reinterpret_cast<const float4*>(dr)[c4];
+      const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
 #pragma unroll
-  for (int c = 0; c < CMAX; ++c) part[rg][c][lane] = acc[c];
-  __syncthreads();
-  if (rg == 0 && f < F) {
-#pragma unroll
-    for (int c = 0; c < CMAX; ++c) {
-      if (c < C) {
-        float t = 0.f;
-        for (int q = 0; q < kWgRowGroups; ++q) t += part[q][c][lane];
-        dW[c * F + f] = t;
+      for (int q = 0; q < 4; ++q) {
+        const int c = 4 * c4 + q;
+        if (c < C) {
+          acc[c].x = fmaf(gv[q], p.x, acc[c].x);
+          acc[c].y = fmaf(gv[q], p.y, acc[c].y);
+          acc[c].z = fmaf(gv[q], p.z, acc[c].z);
+          acc[c].w = fmaf(gv[q], p.w, acc[c].w);
+        }
       }
     }
+  };
+  for (int64_t r0 = rbeg; r0 < rend; r0 += kWgChunk) {
+    const int rows = (int)((rend - r0) < kWgChunk ? (rend - r0) : kWgChunk);
+    __syncthreads();  // the previous chunk is consumed
+    for (int i = threadIdx.x; i < rows * C4; i += blockDim.x) {
+      const int r = i / C4, c = i % C4;
+      dls[i] = c < C ? dl[(r0 + r) * C + c] : 0.f;
+    }
+    __syncthreads();
+    if (!active) continue;
+    int i = rg;
+    for (; i + (kWgUnroll - 1) * kWgRowGroups < rows; i += kWgUnroll * kWgRowGroups) {
+      float4 p[kWgUnroll];
+#pragma unroll
+      for (int u = 0; u < kWgUnroll; ++u)
+        p[u] = __ldg(reinterpret_cast<const float4*>(phi + (r0 + i + u * kWgRowGroups) * F + f));
+#pragma unroll
+      for (int u = 0; u < kWgUnroll; ++u) fma_row(p[u], dls + (i + u * kWgRowGroups) * C4);
+    }
+    for (; i < rows; i += kWgRowGroups)
+      fma_row(__ldg(reinterpret_cast<const float4*>(phi + (r0 + i) * F + f)), dls + i * C4);
   }
+  // Per class, warp 0 adds the 8 warp sums into bsum[c]; then, after one
+  // cluster barrier, warp w of rank 0 adds classes w, w + 8 over the ranks.
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    part[rg][lane] = acc[c];
+    __syncthreads();
+    if (rg == 0) {
+      float4 t = part[0][lane];
+      for (int q = 1; q < kWgRowGroups; ++q) {
+        const float4 v = part[q][lane];
+        t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w;
+      }
+      bsum[c][lane] = t;
+    }
+    __syncthreads();  // part is free for the next class
+  }
+  cluster.sync();  // every block's sums are in place
+  if (ry == 0 && active) {
+    for (int c = rg; c < C; c += kWgRowGroups) {
+      float4 t = bsum[c][lane];
+      for (int q = 1; q < RS; ++q) {
+        const float4 v = cluster.map_shared_rank(&bsum[0][0], q)[c * 32 + lane];
+        t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w;
+      }
+      float* o = dW + c * F + f;  // dW may be only 4-byte aligned
+      o[0] = t.x;
+      o[1] = t.y;
+      o[2] = t.z;
+      o[3] = t.w;
+    }
+  }
+  cluster.sync();  // no block leaves while rank 0 still reads its bsum
 }
 
-__global__ void k_bias_grads(const float* __restrict__ dl, int64_t n, int C, float* __restrict__ db) {
-  const int c = threadIdx.x;
-  if (c >= C) return;
-  float s = 0.f;
-  for (int64_t i = 0; i < n; ++i) s += dl[i * C + c];
-  db[c] = s;
+template <int C>
+cudaError_t run_weight_grads(const float* dlogits, const float* phi, int64_t n, int64_t F,
+                             float* dW, cudaStream_t s) {
+  // Row ranges per column range: the fewest (a power of two up to the
+  // portable cluster size 8) that give two blocks per SM, each with at least
+  // 64 rows.
+  const int64_t cols = (F + 127) / 128;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
+  int rs = 1;
+  while (rs < 8 && cols * rs < 2ll * sms && n / (2 * rs) >= 64) rs *= 2;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)cols, (unsigned)rs, 1);
+  cfg.blockDim = dim3(32 * kWgRowGroups, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = (unsigned)rs;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t err = cudaLaunchKernelEx(&cfg, k_weight_grads<C>, dlogits, phi, n, F, dW);
+  if (err != cudaSuccess) return err;
+  return cudaGetLastError();
+}
+
+// db[c] = sum_n dlogits[n][c]: thread t sums rows t, t + 256, ... and the 256
+// partial sums are added pairwise in a fixed tree.
+__global__ void __launch_bounds__(256) k_bias_grads(const float* __restrict__ dl, int64_t n, int C,
+                                                    float* __restrict__ db) {
+  __shared__ float red[256];
+  for (int c = 0; c < C; ++c) {
+    float s = 0.f;
+    for (int64_t i = threadIdx.x; i < n; i += 256) s += dl[i * C + c];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+      if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) db[c] = red[0];
+    __syncthreads();
+  }
 }
 
 template <int L, bool FUSED>
 cudaError_t run_bwd(const BwdLaunch& P0, int64_t num_partials, cudaStream_t s) {
   BwdLaunch P = P0;
   const FeatureArgs& a = P.b.f;
-  const size_t smem = sizeof(BwdSmem<L>) * kBW;
+  const size_t smem_i = sizeof(BwdSmem<L, false>) * kBW;
   cudaError_t err;
   if (P.b.dCs || P.b.dG || P.b.phi_out) {
+    size_t smem_p = sizeof(BwdBlockSmem<L>);
+    const size_t wbytes = FUSED ? sizeof(float) * (size_t)P.b.C * 2 * ((size_t)1 << L) : 0;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      optin = 0;
+    P.w_smem = FUSED && smem_p + wbytes <= (size_t)optin;
+    if (P.w_smem) smem_p += wbytes;
     err = cudaFuncSetAttribute(k_bwd_params<L, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
+                               (int)smem_p);
     if (err != cudaSuccess) return err;
-    P.wpe = (int)(num_partials / a.E);
-    const unsigned grid = (unsigned)((num_partials + kBW - 1) / kBW);
-    k_bwd_params<L, FUSED><<<grid, kBW * 32, smem, s>>>(P, num_partials);
+    P.bpe = (int)(num_partials / a.E);
+    k_bwd_params<L, FUSED><<<(unsigned)num_partials, kBP * 32, smem_p, s>>>(P);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if (P.b.dCs || P.b.dG) {
-      const int64_t total = (int64_t)a.E << L;
-      k_reduce_params<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
-          P.partials, (int64_t)1 << L, a.E, P.wpe, P.b.dCs, P.b.dG);
+      const int cols = std::min(kRpCols, (1 << L) / 4);
+      const unsigned blocks = (unsigned)(((int64_t)a.E << L) / (4 * cols));
+      k_reduce_params<<<blocks, kRpCols * kRpGroups, 0, s>>>(
+          P.partials, (int64_t)1 << L, a.E, P.bpe, P.b.dCs, P.b.dG);
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
   }
   if (P.b.dx) {
     err = cudaFuncSetAttribute(k_bwd_input<L, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
+                               (int)smem_i);
     if (err != cudaSuccess) return err;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bwd_input<L, FUSED>, kBW * 32, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bwd_input<L, FUSED>, kBW * 32, smem_i) !=
         cudaSuccess)
       occ = 1;
     occ = std::max(occ, 1);
@@ -464,7 +762,7 @@ cudaError_t run_bwd(const BwdLaunch& P0, int64_t num_partials, cudaStream_t s) {
     const int64_t need = (steps + kBW - 1) / kBW;
     const unsigned grid =
         (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)a.num_sms * occ));
-    k_bwd_input<L, FUSED><<<grid, kBW * 32, smem, s>>>(P);
+    k_bwd_input<L, FUSED><<<grid, kBW * 32, smem_i, s>>>(P);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   return cudaSuccess;
@@ -491,6 +789,14 @@ cudaError_t launch_softmax_xent(const float* logits, const int32_t* labels, int6
   return cudaGetLastError();
 }
 
+int64_t backward_partials(int L, int64_t n, int E, int num_sms) {
+  const int vpw = 32 >> (L - 5);
+  const int64_t units = (n + vpw - 1) / vpw;
+  int64_t bpe = num_sms / E;
+  bpe = std::max<int64_t>(1, std::min<int64_t>(bpe, units / kBP));
+  return bpe * E;
+}
+
 cudaError_t launch_backward(const BackwardArgs& b, float* partials, int64_t num_partials,
                             cudaStream_t s) {
   if (b.f.n == 0) return cudaSuccess;
@@ -505,12 +811,29 @@ cudaError_t launch_backward(const BackwardArgs& b, float* partials, int64_t num_
 cudaError_t launch_logit_weight_grads(const float* dlogits, const float* phi, int64_t n, int C,
                                       int64_t F, float* dW, float* db, cudaStream_t s) {
   if (dW) {
-    k_weight_grads<<<(unsigned)((F + 31) / 32), 32 * kWgRowGroups, 0, s>>>(dlogits, phi, n, C, F, dW);
-    cudaError_t err = cudaGetLastError();
+    cudaError_t err;
+    switch (C) {
+      case 1: err = run_weight_grads<1>(dlogits, phi, n, F, dW, s); break;
+      case 2: err = run_weight_grads<2>(dlogits, phi, n, F, dW, s); break;
+      case 3: err = run_weight_grads<3>(dlogits, phi, n, F, dW, s); break;
+      case 4: err = run_weight_grads<4>(dlogits, phi, n, F, dW, s); break;
+      case 5: err = run_weight_grads<5>(dlogits, phi, n, F, dW, s); break;
+      case 6: err = run_weight_grads<6>(dlogits, phi, n, F, dW, s); break;
+      case 7: err = run_weight_grads<7>(dlogits, phi, n, F, dW, s); break;
+      case 8: err = run_weight_grads<8>(dlogits, phi, n, F, dW, s); break;
+      case 9: err = run_weight_grads<9>(dlogits, phi, n, F, dW, s); break;
+      case 10: err = run_weight_grads<10>(dlogits, phi, n, F, dW, s); break;
+      case 11: err = run_weight_grads<11>(dlogits, phi, n, F, dW, s); break;
+      case 12: err = run_weight_grads<12>(dlogits, phi, n, F, dW, s); break;
+      case 13: err = run_weight_grads<13>(dlogits, phi, n, F, dW, s); break;
+      case 14: err = run_weight_grads<14>(dlogits, phi, n, F, dW, s); break;
+      case 15: err = run_weight_grads<15>(dlogits, phi, n, F, dW, s); break;
+      default: err = run_weight_grads<16>(dlogits, phi, n, F, dW, s); break;
+    }
     if (err != cudaSuccess) return err;
   }
   if (db) {
-    k_bias_grads<<<1, 32, 0, s>>>(dlogits, n, C, db);
+    k_bias_grads<<<1, 256, 0, s>>>(dlogits, n, C, db);
     return cudaGetLastError();
   }
   return cudaSuccess;

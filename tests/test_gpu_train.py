@@ -27,8 +27,13 @@ def _rel(got, ref):
 
 @pytest.mark.parametrize("d,E,C,n", [(8, 2, 10, 5), (64, 2, 3, 9), (1024, 2, 10, 17),
                                      (1024, 3, 16, 8), (1024, 2, 1, 9), (1024, 2, 9, 23),
-                                     (1024, 1, 8, 1), (2048, 1, 1, 3), (256, 4, 7, 33)])
+                                     (1024, 1, 8, 1), (2048, 1, 1, 3), (256, 4, 7, 33),
+                                     (1024, 16, 10, 100), (1024, 3, 10, 1300)])
 def test_fused_logits(mck, dev, d, E, C, n):
+    # At d = 1024 a batch with fewer 8-row tiles than SMs splits the
+    # expansions into chunks (n = 100: 13 tiles, uneven chunks of E = 16);
+    # n = 1300 has more tiles than SMs, a ragged last tile and blocks that
+    # take two tiles.
     plan = mck.Plan(d, E, "rbf", 1.0, 3)
     x = wl.mnist_like(n, min(d, 784), seed=d)
     W, _ = wl.logit_weights(C, 2 * E * d, seed=1, std=0.05)
@@ -84,8 +89,11 @@ def test_features_backward(mck, dev, d, E, n):
     assert _rel(dg.cpu().numpy(), rdg) < 1e-4
 
 
-@pytest.mark.parametrize("d,E,C,n", [(64, 2, 3, 6), (1024, 2, 10, 11)])
+@pytest.mark.parametrize("d,E,C,n", [(64, 2, 3, 6), (1024, 2, 10, 11), (64, 2, 3, 1100),
+                                     (32, 3, 16, 300)])
 def test_fused_logits_backward(mck, dev, d, E, C, n):
+    # n = 1100 at d = 64 splits dW's rows over a cluster of 8 blocks (ragged
+    # ranges); d = 32 reduces dCs/dG over 8 float4 columns per block.
     plan = mck.Plan(d, E, "rbf", 1.0, 23)
     x = wl.mnist_like(n, min(d, 784), seed=5)
     W, b = wl.logit_weights(C, 2 * E * d, seed=6, std=0.05)

@@ -35,7 +35,7 @@ def test_noalloc_matches_allocating_entry_point_twice(mck, dev):
 
     lib = _lib.load()
     # d = 512 runs the fused-logits path that keeps per-(sample, expansion)
-    # partial logits in scratch (d = 1024 reduces inside the kernel instead).
+    # partial logits in scratch.
     plan = mck.Plan(512, 4, "rbf", 1.0, 42)
     C = 10
     W = torch.from_numpy(wl.logit_weights(C, plan.num_features, seed=3, std=0.05)[0]).to(dev)
@@ -50,6 +50,27 @@ def test_noalloc_matches_allocating_entry_point_twice(mck, dev):
         torch.cuda.synchronize()
         err = (got - ref).abs().max().item()
         assert err <= TOL, (call, err)
+
+
+def test_noalloc_small_batch_at_d1024_matches(mck, dev):
+    """d = 1024 with fewer 8-row tiles than SMs splits the expansions into
+    chunks whose partial logits also live in the fixed array."""
+    from paper_1702_08159_gb300 import _lib
+
+    lib = _lib.load()
+    plan = mck.Plan(1024, 16, "rbf", 3.0, 7)
+    C = 10
+    W = torch.from_numpy(wl.logit_weights(C, plan.num_features, seed=5)[0]).to(dev)
+    b = torch.linspace(-1, 1, C, device=dev)
+    for n in (512, 37):
+        x = torch.from_numpy(wl.mnist_like(n, 784, seed=n)).to(dev)
+        ref = torch.empty((n, C), device=dev)
+        got = torch.full((n, C), float("nan"), device=dev)
+        assert _call(lib, "mck_fused_logits", plan, x, W, b, ref) == 0
+        assert _call(lib, "mck_fused_logits_noalloc", plan, x, W, b, got) == 0, \
+            lib.mck_last_error()
+        torch.cuda.synchronize()
+        assert torch.equal(got, ref), n  # same kernels, same order of sums
 
 
 def test_noalloc_refuses_oversized_batch(mck, dev):
