@@ -579,23 +579,25 @@ __global__ void __launch_bounds__(kRpCols * kRpGroups) k_reduce_params(
 // the result does not depend on scheduling.
 constexpr int kWgRowGroups = 8;
 constexpr int kWgChunk = 256;  // rows of dlogits staged per pass
-constexpr int kWgUnroll = 8;   // rows in flight per warp
 
 template <int C>
-__global__ void __launch_bounds__(32 * kWgRowGroups) k_weight_grads(const float* __restrict__ dl,
+__global__ void __launch_bounds__(32 * kWgRowGroups, 2) k_weight_grads(const float* __restrict__ dl,
                                                                    const float* __restrict__ phi,
                                                                    int64_t n, int64_t F,
-                                                                   float* __restrict__ dW) {
+                                                                   float* __restrict__ dW,
+                                                                   float* __restrict__ db) {
   constexpr int C4 = (C + 3) / 4 * 4;  // padded row of dlogits in shared memory
+  constexpr int kWgUnroll = C <= 10 ? 16 : 8;  // rows in flight per warp (registers allowing)
   __shared__ float4 dls4[kWgChunk * C4 / 4];
   __shared__ float4 part[kWgRowGroups][32];
   __shared__ float4 bsum[C][32];
+  __shared__ float4 bias4[C4 / 4];
   float* dls = reinterpret_cast<float*>(dls4);
   cg::cluster_group cluster = cg::this_cluster();
   const int RS = (int)gridDim.y, ry = (int)blockIdx.y;  // cluster = the RS blocks of a column
   const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;
   const int64_t f = ((int64_t)blockIdx.x * 32 + lane) * 4;  // F is a multiple of 4
-  const bool active = f < F;
+  const bool active = dW && f < F;  // without dW only column block 0 runs, for db
   const int64_t rbeg = n * ry / RS, rend = n * (ry + 1) / RS;
   float4 acc[C];
 #pragma unroll
@@ -617,14 +619,29 @@ __global__ void __launch_bounds__(32 * kWgRowGroups) k_weight_grads(const float*
       }
     }
   };
+  float4 bacc = make_float4(0.f, 0.f, 0.f, 0.f);  // column block 0: db partial sums
   for (int64_t r0 = rbeg; r0 < rend; r0 += kWgChunk) {
     const int rows = (int)((rend - r0) < kWgChunk ? (rend - r0) : kWgChunk);
     __syncthreads();  // the previous chunk is consumed
-    for (int i = threadIdx.x; i < rows * C4; i += blockDim.x) {
-      const int r = i / C4, c = i % C4;
-      dls[i] = c < C ? dl[(r0 + r) * C + c] : 0.f;
+    {  // all of a thread's loads first, then the stores (one latency, not C4)
+      static_assert(kWgChunk == 32 * kWgRowGroups, "one padded row per thread and pass");
+      float v[C4];
+#pragma unroll
+      for (int k = 0; k < C4; ++k) {
+        const int i = threadIdx.x + k * kWgChunk, r = i / C4, c = i % C4;
+        v[k] = (r < rows && c < C) ? __ldg(dl + (r0 + r) * C + c) : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < C4; ++k) dls[threadIdx.x + k * kWgChunk] = v[k];
     }
     __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x < C4 / 4) {  // db: this range's rows, in order
+#pragma unroll 8
+      for (int r = 0; r < rows; ++r) {
+        const float4 g4 = dls4[r * (C4 / 4) + threadIdx.x];
+        bacc.x += g4.x; bacc.y += g4.y; bacc.z += g4.z; bacc.w += g4.w;
+      }
+    }
     if (!active) continue;
     int i = rg;
     for (; i + (kWgUnroll - 1) * kWgRowGroups < rows; i += kWgUnroll * kWgRowGroups) {
@@ -654,8 +671,15 @@ __global__ void __launch_bounds__(32 * kWgRowGroups) k_weight_grads(const float*
     }
     __syncthreads();  // part is free for the next class
   }
+  if (blockIdx.x == 0 && threadIdx.x < C4 / 4) bias4[threadIdx.x] = bacc;
   cluster.sync();  // every block's sums are in place
-  if (ry == 0 && active) {
+  if (db && blockIdx.x == 0 && ry == 0 && threadIdx.x < C) {
+    const int c = threadIdx.x;
+    float t = reinterpret_cast<const float*>(bias4)[c];
+    for (int q = 1; q < RS; ++q) t += reinterpret_cast<const float*>(cluster.map_shared_rank(bias4, q))[c];
+    db[c] = t;
+  }
+  if (dW && ry == 0 && active) {
     for (int c = rg; c < C; c += kWgRowGroups) {
       float4 t = bsum[c][lane];
       for (int q = 1; q < RS; ++q) {
@@ -674,16 +698,16 @@ __global__ void __launch_bounds__(32 * kWgRowGroups) k_weight_grads(const float*
 
 template <int C>
 cudaError_t run_weight_grads(const float* dlogits, const float* phi, int64_t n, int64_t F,
-                             float* dW, cudaStream_t s) {
-  // Row ranges per column range: the fewest (a power of two up to the
-  // portable cluster size 8) that give two blocks per SM, each with at least
-  // 64 rows.
-  const int64_t cols = (F + 127) / 128;
+                             float* dW, float* db, cudaStream_t s) {
+  // Row ranges per column range: a power of two up to the portable cluster
+  // size 8, doubled while the grid still fits in one wave of two blocks per
+  // SM and every range keeps at least 128 rows.
+  const int64_t cols = dW ? (F + 127) / 128 : 1;
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
   int rs = 1;
-  while (rs < 8 && cols * rs < 2ll * sms && n / (2 * rs) >= 64) rs *= 2;
+  while (rs < 8 && cols * rs * 2 <= 2ll * sms && n / (2 * rs) >= 128) rs *= 2;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)cols, (unsigned)rs, 1);
   cfg.blockDim = dim3(32 * kWgRowGroups, 1, 1);
@@ -696,28 +720,9 @@ cudaError_t run_weight_grads(const float* dlogits, const float* phi, int64_t n, 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t err = cudaLaunchKernelEx(&cfg, k_weight_grads<C>, dlogits, phi, n, F, dW);
+  cudaError_t err = cudaLaunchKernelEx(&cfg, k_weight_grads<C>, dlogits, phi, n, F, dW, db);
   if (err != cudaSuccess) return err;
   return cudaGetLastError();
-}
-
-// db[c] = sum_n dlogits[n][c]: thread t sums rows t, t + 256, ... and the 256
-// partial sums are added pairwise in a fixed tree.
-__global__ void __launch_bounds__(256) k_bias_grads(const float* __restrict__ dl, int64_t n, int C,
-                                                    float* __restrict__ db) {
-  __shared__ float red[256];
-  for (int c = 0; c < C; ++c) {
-    float s = 0.f;
-    for (int64_t i = threadIdx.x; i < n; i += 256) s += dl[i * C + c];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int h = 128; h > 0; h >>= 1) {
-      if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) db[c] = red[0];
-    __syncthreads();
-  }
 }
 
 template <int L, bool FUSED>
@@ -810,33 +815,25 @@ cudaError_t launch_backward(const BackwardArgs& b, float* partials, int64_t num_
 
 cudaError_t launch_logit_weight_grads(const float* dlogits, const float* phi, int64_t n, int C,
                                       int64_t F, float* dW, float* db, cudaStream_t s) {
-  if (dW) {
-    cudaError_t err;
-    switch (C) {
-      case 1: err = run_weight_grads<1>(dlogits, phi, n, F, dW, s); break;
-      case 2: err = run_weight_grads<2>(dlogits, phi, n, F, dW, s); break;
-      case 3: err = run_weight_grads<3>(dlogits, phi, n, F, dW, s); break;
-      case 4: err = run_weight_grads<4>(dlogits, phi, n, F, dW, s); break;
-      case 5: err = run_weight_grads<5>(dlogits, phi, n, F, dW, s); break;
-      case 6: err = run_weight_grads<6>(dlogits, phi, n, F, dW, s); break;
-      case 7: err = run_weight_grads<7>(dlogits, phi, n, F, dW, s); break;
-      case 8: err = run_weight_grads<8>(dlogits, phi, n, F, dW, s); break;
-      case 9: err = run_weight_grads<9>(dlogits, phi, n, F, dW, s); break;
-      case 10: err = run_weight_grads<10>(dlogits, phi, n, F, dW, s); break;
-      case 11: err = run_weight_grads<11>(dlogits, phi, n, F, dW, s); break;
-      case 12: err = run_weight_grads<12>(dlogits, phi, n, F, dW, s); break;
-      case 13: err = run_weight_grads<13>(dlogits, phi, n, F, dW, s); break;
-      case 14: err = run_weight_grads<14>(dlogits, phi, n, F, dW, s); break;
-      case 15: err = run_weight_grads<15>(dlogits, phi, n, F, dW, s); break;
-      default: err = run_weight_grads<16>(dlogits, phi, n, F, dW, s); break;
-    }
-    if (err != cudaSuccess) return err;
+  if (!dW && !db) return cudaSuccess;
+  switch (C) {
+    case 1: return run_weight_grads<1>(dlogits, phi, n, F, dW, db, s);
+    case 2: return run_weight_grads<2>(dlogits, phi, n, F, dW, db, s);
+    case 3: return run_weight_grads<3>(dlogits, phi, n, F, dW, db, s);
+    case 4: return run_weight_grads<4>(dlogits, phi, n, F, dW, db, s);
+    case 5: return run_weight_grads<5>(dlogits, phi, n, F, dW, db, s);
+    case 6: return run_weight_grads<6>(dlogits, phi, n, F, dW, db, s);
+    case 7: return run_weight_grads<7>(dlogits, phi, n, F, dW, db, s);
+    case 8: return run_weight_grads<8>(dlogits, phi, n, F, dW, db, s);
+    case 9: return run_weight_grads<9>(dlogits, phi, n, F, dW, db, s);
+    case 10: return run_weight_grads<10>(dlogits, phi, n, F, dW, db, s);
+    case 11: return run_weight_grads<11>(dlogits, phi, n, F, dW, db, s);
+    case 12: return run_weight_grads<12>(dlogits, phi, n, F, dW, db, s);
+    case 13: return run_weight_grads<13>(dlogits, phi, n, F, dW, db, s);
+    case 14: return run_weight_grads<14>(dlogits, phi, n, F, dW, db, s);
+    case 15: return run_weight_grads<15>(dlogits, phi, n, F, dW, db, s);
+    default: return run_weight_grads<16>(dlogits, phi, n, F, dW, db, s);
   }
-  if (db) {
-    k_bias_grads<<<1, 256, 0, s>>>(dlogits, n, C, db);
-    return cudaGetLastError();
-  }
-  return cudaSuccess;
 }
 
 }  // namespace mck

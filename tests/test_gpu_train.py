@@ -107,6 +107,23 @@ def test_fused_logits_backward(mck, dev, d, E, C, n):
         assert _rel(g[k].cpu().numpy(), o[k]) < 1e-4, k
 
 
+def test_fused_logits_backward_partial_requests(mck, dev):
+    """db alone (no features recomputed for dW), and dW without db."""
+    plan = mck.Plan(128, 3, "rbf", 1.0, 29)
+    n, C = 300, 5
+    x = wl.mnist_like(n, 100, seed=11)
+    W, b = wl.logit_weights(C, 2 * 3 * 128, seed=12, std=0.05)
+    y = wl.labels(n, C, seed=13)
+    o = tr.train_grads(x.astype(np.float64), _tables(plan), W.astype(np.float64),
+                       b.astype(np.float64), y)
+    xd, Wd = torch.from_numpy(x).to(dev), torch.from_numpy(W).to(dev)
+    dl = torch.from_numpy(o["dlogits"].astype(np.float32)).to(dev)
+    g = mck.fused_logits_backward(plan, xd, Wd, dl, need_dCs=False, need_dG=False, need_dW=False)
+    assert g["dW"] is None and _rel(g["db"].cpu().numpy(), o["db"]) < 1e-5
+    g = mck.fused_logits_backward(plan, xd, Wd, dl, need_db=False)
+    assert g["db"] is None and _rel(g["dW"].cpu().numpy(), o["dW"]) < 1e-4
+
+
 def test_training_step_config3_shape(mck, dev):
     # N=512, d=1024 (784 padded), E=16, 10 classes, learnable C and G, uniform labels.
     from paper_1702_08159_gb300.autograd import McKernelClassifier
