@@ -63,7 +63,7 @@ def parse():
     p.add_argument("--batch", type=int, default=N,
                    help="rows per GPU (default 60000; smaller values are for profiling captures)")
     p.add_argument("--legs", default="all",
-                   help="comma list of extra legs to run (e2e,logits,train,sweep,uneven,configs01) or 'all'")
+                   help="comma list of extra legs to run (e2e,logits,train,sweep,uneven,configs01,fsweep) or 'all'")
     p.add_argument("--uneven-count", type=int, default=10000,
                    help="vectors in the config-4 leg (smaller values are for profiling captures)")
     return p.parse_args()
@@ -302,7 +302,7 @@ def main():
 
     if not args.no_extras:
         legs = set(args.legs.split(",")) if args.legs != "all" else {
-            "e2e", "logits", "train", "sweep", "uneven", "configs01"}
+            "e2e", "logits", "train", "sweep", "uneven", "configs01", "fsweep"}
         if "e2e" in legs:
             line["e2e"] = e2e_leg(mck, plan, x_host, dev, stream, world)
         if "logits" in legs:
@@ -313,6 +313,8 @@ def main():
             line["fwht_sweep"] = fwht_sweep_leg(mck, dev, stream, args)
         if "uneven" in legs:
             line["uneven_batch"] = uneven_leg(mck, dev, stream, args)
+        if "fsweep" in legs:
+            line["feature_sweep"] = feature_sweep_leg(mck, dev, stream, args)
         if "configs01" in legs:
             line["configs01"] = configs01_leg(mck, dev, stream, args)
     del phi
@@ -503,6 +505,40 @@ def configs01_leg(mck, dev, stream, args):
                                   "ms_fused_logits": ml, "logit_rows_per_s": N / (ml / 1e3)}
         pl.close()
     del f1, x1
+    return out
+
+
+def feature_sweep_leg(mck, dev, stream, args):
+    """Batched feature kernels across d: RBF plans with E = 4, N(0,1) rows of
+    length d, the batch sized to 1 GiB of features; mean CUDA-event time of a
+    launch and GB/s of algorithmic traffic (x read once, features written)."""
+    import torch
+
+    import workloads as wl
+
+    out = []
+    for L in range(5, 16):
+        d, E = 1 << L, 4
+        n = max(1, (1 << 28) // (2 * E * d))
+        plan = mck.Plan(d, E, "rbf", 1.0, SEED)
+        x = torch.from_numpy(wl.gaussian(n, d, seed=SEED + L)).to(dev)
+        phi = torch.empty((n, 2 * E * d), device=dev)
+        for _ in range(3):
+            mck.features(plan, x, out=phi)
+        torch.cuda.synchronize()
+        reps = 5
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            mck.features(plan, x, out=phi)
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(e) / reps
+        gbs = n * (d + 2 * E * d) * 4 / (ms / 1e3) / 1e9
+        out.append({"d": d, "E": E, "rows": n, "ms": ms, "gbs": gbs,
+                    "frac_of_measured_hbm": gbs / measured_peaks()[0]})
+        plan.close()
+        del x, phi
     return out
 
 
