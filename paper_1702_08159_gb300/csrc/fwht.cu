@@ -9,9 +9,14 @@
 //               warp): register phases A and B with one shared-memory layout
 //               move in between, 128-bit coalesced global loads and stores.
 //   L = 11..15  one block of 2^(L-5) threads per vector: phases A, B, C.
-//   L = 16..20  two passes over HBM: the L = 15 kernel on every 2^15 block
+//   L = 16, 17  one pass: a thread-block cluster of 2^(L-15) blocks per
+//               vector; each block transforms a 2^15 slice, then the rank
+//               bits are transformed across the cluster through distributed
+//               shared memory on the way out to HBM.
+//   L = 18..20  two passes over HBM: the L = 15 kernel on every 2^15 block
 //               (index bits 0..14), then a column pass over bits 15..L-1.
 // Every element is read and written once per pass.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -21,6 +26,8 @@
 
 namespace mck {
 namespace {
+
+namespace cg = cooperative_groups;
 
 constexpr int kWarpsPerBlock = 4;
 
@@ -162,6 +169,63 @@ __global__ void __launch_bounds__(256) k_fwht_columns(float* __restrict__ x, int
   }
 }
 
+// One vector of 2^(LS + log2 CS) per thread-block cluster of CS blocks
+// (single pass over HBM). Block r of the cluster loads slice r (index bits
+// 0..LS-1 local, bits LS.. = r), transforms the local bits in registers and
+// shared memory (phases A, B, C), and leaves the slice in shared memory in
+// natural order. After a cluster barrier, block r takes 1/CS of the local
+// indices: for each it reads the CS slices' values at that index through
+// distributed shared memory, applies H_CS (the rank bits) and writes the CS
+// results to HBM. A second cluster barrier keeps the slices alive until every
+// block has read them.
+template <int LS, int CS>
+__global__ void __launch_bounds__(1 << (LS - 5)) k_fwht_cluster(float* __restrict__ x, int64_t n) {
+  using Y = Lay<LS>;
+  constexpr int S = Y::d, T = Y::T, OWN = S / CS, PER = OWN / T;
+  static_assert(LS >= 11 && PER * CS == 32, "cluster slices");
+  extern __shared__ float4 sm4[];
+  float* buf = reinterpret_cast<float*>(sm4);
+  cg::cluster_group cl = cg::this_cluster();
+  const int r = (int)cl.block_rank();
+  const int lam = threadIdx.x;
+  const int64_t ncl = gridDim.x / CS;
+  for (int64_t v = blockIdx.x / CS; v < n; v += ncl) {
+    float* row = x + v * (int64_t)(S * CS);
+    float w[32];
+    gload_A<LS>(row + (int64_t)r * S, lam, true, w);
+    hreg<Y::maskA()>(w);
+    store_A<LS>(buf, 0, lam, w);
+    __syncthreads();
+    load_B<LS>(buf, 0, lam, w);
+    hreg<Y::maskB()>(w);
+    store_B<LS>(buf, 0, lam, w);
+    __syncthreads();
+    load_C<LS>(buf, lam, w);
+    hreg<Y::maskC()>(w);
+    store_C<LS>(buf, lam, w);
+    cl.sync();  // every slice is transformed over its local bits
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int i = r * OWN + q * T + lam;
+      float u[CS];
+#pragma unroll
+      for (int c = 0; c < CS; ++c) u[c] = cl.map_shared_rank(buf, c)[pad(i)];
+#pragma unroll
+      for (int h = 1; h < CS; h <<= 1)
+#pragma unroll
+        for (int c = 0; c < CS; ++c)
+          if (!(c & h)) {
+            const float a = u[c], b = u[c | h];
+            u[c] = a + b;
+            u[c | h] = a - b;
+          }
+#pragma unroll
+      for (int c = 0; c < CS; ++c) __stcs(row + (int64_t)c * S + i, u[c]);
+    }
+    cl.sync();  // no slice is overwritten while another block still reads it
+  }
+}
+
 template <class K>
 int occupancy_blocks(K kernel, int threads, size_t smem) {
   int b = 0;
@@ -210,6 +274,39 @@ cudaError_t run_columns(float* x, int64_t n, int num_sms, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int LS, int CS>
+cudaError_t run_cluster(float* x, int64_t n, cudaStream_t s) {
+  auto kern = k_fwht_cluster<LS, CS>;
+  const size_t smem = sizeof(float) * Lay<LS>::SLOT;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  if (CS > 8) {
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (err != cudaSuccess) return err;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.blockDim = dim3(Lay<LS>::T, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(CS, 1, 1);
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess || clusters < 1) {
+    cudaGetLastError();
+    return cudaErrorInvalidConfiguration;
+  }
+  cfg.gridDim = dim3((unsigned)(CS * std::min<int64_t>(n, clusters)), 1, 1);
+  err = cudaLaunchKernelEx(&cfg, kern, x, n);
+  if (err != cudaSuccess) return err;
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_fwht(float* x, int64_t n, int L, int num_sms, cudaStream_t s) {
@@ -233,6 +330,11 @@ cudaError_t launch_fwht(float* x, int64_t n, int L, int num_sms, cudaStream_t s)
     default: break;
   }
   if (L > 20) return cudaErrorInvalidValue;
+  // One pass on a cluster of 2 or 4 blocks of 2^15 (measured faster than two
+  // passes there); beyond, clusters of 8 or 16 whole-SM blocks pack the GPCs
+  // poorly and the two passes are as fast or faster.
+  if (L == 16) return run_cluster<15, 2>(x, n, s);
+  if (L == 17) return run_cluster<15, 4>(x, n, s);
   const int64_t blocks = n << (L - 15);
   cudaError_t err = run_cta<15>(x, blocks, num_sms, s);
   if (err != cudaSuccess) return err;

@@ -37,7 +37,7 @@ def test_fwht_one_pass_sizes(mck, dev, L, n):
 
 
 @pytest.mark.parametrize("L,n", [(16, 3), (17, 2), (18, 1), (19, 1), (20, 2)])
-def test_fwht_two_pass_sizes(mck, dev, L, n):
+def test_fwht_large_sizes(mck, dev, L, n):
     d = 1 << L
     x = wl.gaussian(n, d, seed=L)
     t = torch.from_numpy(x).to(dev)
@@ -63,9 +63,12 @@ def test_fwht_basis_vectors_exact(mck, dev):
     np.testing.assert_array_equal(t.cpu().numpy(), ff.sylvester(d))
 
 
-def test_fwht_config2_batch_sampled(mck, dev):
-    # The sweep's batch shape (1 GiB of float32 at d = 2^14), checked on sampled rows.
-    d = 1 << 14
+@pytest.mark.parametrize("L", [14, 16, 17, 20])
+def test_fwht_config2_batch_sampled(mck, dev, L):
+    # The sweep's batch shape (1 GiB of float32), checked on sampled rows: at
+    # d = 2^16 and 2^17 the clusters loop over many vectors (one pass through
+    # distributed shared memory), at 2^20 two passes over HBM.
+    d = 1 << L
     n = (1 << 28) // d
     host = wl.gaussian(n, d, seed=42)
     x = torch.from_numpy(host).to(dev)
