@@ -174,15 +174,15 @@ __global__ void __launch_bounds__(256) k_fwht_columns(float* __restrict__ x, int
 // 0..LS-1 local, bits LS.. = r), transforms the local bits in registers and
 // shared memory (phases A, B, C), and leaves the slice in shared memory in
 // natural order. After a cluster barrier, block r takes 1/CS of the local
-// indices: for each it reads the CS slices' values at that index through
-// distributed shared memory, applies H_CS (the rank bits) and writes the CS
-// results to HBM. A second cluster barrier keeps the slices alive until every
+// indices, four consecutive at a time: it reads the CS slices' values there
+// through distributed shared memory (128-bit), applies H_CS (the rank bits)
+// and writes the CS results to HBM (128-bit, coalesced). A second cluster barrier keeps the slices alive until every
 // block has read them.
 template <int LS, int CS>
 __global__ void __launch_bounds__(1 << (LS - 5)) k_fwht_cluster(float* __restrict__ x, int64_t n) {
   using Y = Lay<LS>;
-  constexpr int S = Y::d, T = Y::T, OWN = S / CS, PER = OWN / T;
-  static_assert(LS >= 11 && PER * CS == 32, "cluster slices");
+  constexpr int S = Y::d, T = Y::T, OWN = S / CS, PER4 = OWN / (4 * T);
+  static_assert(LS >= 11 && PER4 * 4 * CS == 32, "cluster slices (2 <= CS <= 8)");
   extern __shared__ float4 sm4[];
   float* buf = reinterpret_cast<float*>(sm4);
   cg::cluster_group cl = cg::this_cluster();
@@ -205,22 +205,24 @@ __global__ void __launch_bounds__(1 << (LS - 5)) k_fwht_cluster(float* __restric
     store_C<LS>(buf, lam, w);
     cl.sync();  // every slice is transformed over its local bits
 #pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int i = r * OWN + q * T + lam;
-      float u[CS];
+    for (int q = 0; q < PER4; ++q) {
+      const int i = r * OWN + 4 * (q * T + lam);  // four consecutive local indices
+      float4 u[CS];
 #pragma unroll
-      for (int c = 0; c < CS; ++c) u[c] = cl.map_shared_rank(buf, c)[pad(i)];
+      for (int c = 0; c < CS; ++c)
+        u[c] = *reinterpret_cast<const float4*>(cl.map_shared_rank(buf, c) + pad(i));
 #pragma unroll
       for (int h = 1; h < CS; h <<= 1)
 #pragma unroll
         for (int c = 0; c < CS; ++c)
           if (!(c & h)) {
-            const float a = u[c], b = u[c | h];
-            u[c] = a + b;
-            u[c | h] = a - b;
+            const float4 a = u[c], b = u[c | h];
+            u[c] = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+            u[c | h] = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
           }
 #pragma unroll
-      for (int c = 0; c < CS; ++c) __stcs(row + (int64_t)c * S + i, u[c]);
+      for (int c = 0; c < CS; ++c)
+        __stcs(reinterpret_cast<float4*>(row + (int64_t)c * S + i), u[c]);
     }
     cl.sync();  // no slice is overwritten while another block still reads it
   }
@@ -330,9 +332,9 @@ cudaError_t launch_fwht(float* x, int64_t n, int L, int num_sms, cudaStream_t s)
     default: break;
   }
   if (L > 20) return cudaErrorInvalidValue;
-  // One pass on a cluster of 2 or 4 blocks of 2^15 (measured faster than two
-  // passes there); beyond, clusters of 8 or 16 whole-SM blocks pack the GPCs
-  // poorly and the two passes are as fast or faster.
+  // One pass on a cluster of 2 or 4 blocks of 2^15 (54% and 49% of the copy
+  // bandwidth, against 33% and 37% for two passes); a cluster of 8 whole-SM
+  // blocks packs the GPCs poorly and measured slower than two passes.
   if (L == 16) return run_cluster<15, 2>(x, n, s);
   if (L == 17) return run_cluster<15, 4>(x, n, s);
   const int64_t blocks = n << (L - 15);
