@@ -241,13 +241,18 @@ __device__ void block_item(const GArgs& a, const GItem& it, float* buf, int lam,
 __global__ void __launch_bounds__(kGThreads, 1) k_grouped(const GArgs a) {
   extern __shared__ float4 sm4[];
   float* smem = reinterpret_cast<float*>(sm4);
-  __shared__ int s_unit;
+  __shared__ int s_unit[2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (;;) {
-    if (threadIdx.x == 0) s_unit = atomicAdd(a.counter, 1);
-    __syncthreads();
-    const int64_t u = s_unit;
+  if (threadIdx.x == 0) s_unit[0] = atomicAdd(a.counter, 1);
+  __syncthreads();
+  // The next unit's index is requested while the current unit runs (thread 0
+  // holds the pending result in a register and publishes it at the end), so
+  // the atomic's round trip is hidden behind the work.
+  for (int cur = 0;; cur ^= 1) {
+    const int64_t u = s_unit[cur];
     if (u >= a.num_units) break;
+    int next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(a.counter, 1);
     const GUnit unit = a.units[u];
     if (unit.type == 0) {
       float* buf = smem + warp * kWarpBuf;
@@ -279,6 +284,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_grouped(const GArgs a) {
         }
       }
     }
+    if (threadIdx.x == 0) s_unit[cur ^ 1] = next;
     __syncthreads();
   }
 }
