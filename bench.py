@@ -288,6 +288,24 @@ def main():
                 "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
                 "kernel": "k_feat_warp<10,0>", "bytes_per_launch": nb * bytes_per_row,
                 "traffic": ncu_traffic("k_feat_warp<10,0>")}
+    # Context for the write-dominated kernel: what a plain store stream reaches
+    # on this GPU (torch's fill of the same output buffer, no reads), outside
+    # the timed region.
+    for _ in range(3):
+        phi.fill_(0.5)
+    torch.cuda.synchronize()
+    fill_ms = []
+    for _ in range(5):
+        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_ev.record(stream)
+        phi.fill_(0.5)
+        b_ev.record(stream)
+        torch.cuda.synchronize()
+        fill_ms.append(a_ev.elapsed_time(b_ev))
+    wgbs = phi.numel() * 4 / (statistics.median(fill_ms) / 1e3) / 1e9
+    roofline["write_only_reference"] = {
+        "gbs": wgbs, "frac_of_peak": wgbs / peak, "kernel": "torch Tensor.fill_ of the output buffer",
+        "bytes": phi.numel() * 4, "feature_kernel_achieved_over_it": achieved / wgbs}
 
     line = {"metric": METRIC, "value": value, "unit": "features/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
