@@ -92,6 +92,7 @@ struct BwdLaunch {
   float* partials;  // [E][bpe][2][d]
   int bpe;          // blocks per expansion (k_bwd_params)
   bool w_smem;      // k_bwd_params stages W_e in shared memory
+  bool d_tile;      // k_bwd_params forms dphi for kBP rows at a time in shared memory (d = 1024)
 };
 
 __device__ __forceinline__ void apply_signs(float (&w)[32], uint32_t mask) {
@@ -125,6 +126,7 @@ struct BwdTabs {
   float* gl;   // per-lane G in layout B, or null: read G from global
   float* csl;  // per-lane Cs in layout A, or null: read Cs from global
   uint32_t ws;       // shared address of W_e (C x 2d), or 0: read W from global
+  uint32_t dt;       // shared address of the sample's dphi row (2d), formed by the block, or 0
 };
 
 // Tables of expansion e held in registers for the warp's samples: B as a bit
@@ -260,7 +262,15 @@ __device__ __forceinline__ void bwd_core(const BwdLaunch& P, const BwdTabs& tb, 
   // dphi for the lane's elements: from memory, or formed as W_e^T dlogits
   // class by class (64 accumulators, one dlogits value per class).
   float dc[32], ds[32];
-  if constexpr (FUSED) {
+  if (FUSED && tb.dt) {  // the row the block formed in shared memory
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const uint32_t at = tb.dt + 4u * (uint32_t)Y::kA(lam, 4 * m);
+      const float4 vc = lds128(at), vs = lds128(at + 4u * d);
+      dc[4 * m] = vc.x; dc[4 * m + 1] = vc.y; dc[4 * m + 2] = vc.z; dc[4 * m + 3] = vc.w;
+      ds[4 * m] = vs.x; ds[4 * m + 1] = vs.y; ds[4 * m + 2] = vs.z; ds[4 * m + 3] = vs.w;
+    }
+  } else if constexpr (FUSED) {
     for (int c = lam; c < P.b.C; c += Y::T)  // dlogits of sample n, shared by its group's lanes
       S.dl[g * CMAX + c] = valid ? __ldg(P.b.dlogits + n * P.b.C + c) : 0.f;
     __syncwarp();
@@ -418,7 +428,7 @@ __global__ void __launch_bounds__(kBP * 32, 1) k_bwd_params(const BwdLaunch P) {
   // ---- stage the expansion's tables ----
   if (warp == 0) {
     float gt[32];
-    const BwdTabs none{nullptr, nullptr, 0u};  // read G from global
+    const BwdTabs none{nullptr, nullptr, 0u, 0u};  // read G from global
     load_G_B<L>(a, none, e, lam, gt);
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
@@ -427,7 +437,7 @@ __global__ void __launch_bounds__(kBP * 32, 1) k_bwd_params(const BwdLaunch P) {
           __ldg(reinterpret_cast<const float4*>(a.Cs + off + Y::kA(lam, 4 * m)));
     }
   }
-  if (FUSED && P.w_smem) {
+  if (FUSED && P.w_smem && !P.d_tile) {
     const int64_t F = 2ll * a.E * d;
     const int per_class4 = 2 * d / 4;
     for (int i = threadIdx.x; i < P.b.C * per_class4; i += blockDim.x) {
@@ -436,7 +446,7 @@ __global__ void __launch_bounds__(kBP * 32, 1) k_bwd_params(const BwdLaunch P) {
           __ldg(reinterpret_cast<const float4*>(P.b.W + c * F + 2ll * e * d) + f4);
     }
   }
-  const BwdTabs tb{B.gl, B.csl, (FUSED && P.w_smem) ? smem_addr(Wsm) : 0u};
+  BwdTabs tb{B.gl, B.csl, (FUSED && P.w_smem && !P.d_tile) ? smem_addr(Wsm) : 0u, 0u};
   uint32_t bmask;
   uint32_t poff[16];
   load_tables<L>(a, e, lam, bmask, poff);
@@ -446,16 +456,74 @@ __global__ void __launch_bounds__(kBP * 32, 1) k_bwd_params(const BwdLaunch P) {
     lane4(S.dg, m, lane) = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();
-  const int64_t units = (a.n + BS::VPW - 1) / BS::VPW;
-  const int64_t nw = (int64_t)P.bpe * kBP, q = (int64_t)sb * kBP + warp;
-  const int64_t u0 = units * q / nw, u1 = units * (q + 1) / nw;
-  for (int64_t u = u0; u < u1; ++u) {
-    const int64_t n = u * BS::VPW + g;
-    const bool valid = n < a.n;
-    float w[32];
-    // An invalid sample contributes exactly zero: x-hat = 0 gives h = 0,
-    // and its upstream gradient is read as 0 (dphi) or dlogits = 0.
-    bwd_core<L, FUSED, true>(P, tb, n, e, valid, g, lam, S, slot, bmask, poff, w);
+  if constexpr (FUSED && L == 10) {
+    if (P.d_tile) {
+      // The block walks its rows kBP at a time, warp w taking row r0 + w. Per
+      // tile the 256 threads first form dphi = dlogits W_e for all kBP rows
+      // (thread t owns float4 columns t and t + 256: its weights are loaded
+      // once per tile and used for every row), then each warp runs its row.
+      float* dtile = Wsm;                 // [kBP][2d]
+      float* dls = dtile + kBP * 2 * d;   // [kBP][CMAX]
+      const int C = P.b.C;
+      const int64_t F = 2ll * a.E * d;
+      const float* We = P.b.W + 2ll * e * d;
+      const int64_t n0 = a.n * sb / P.bpe, n1 = a.n * (sb + 1) / P.bpe;
+      tb.dt = smem_addr(dtile + warp * 2 * d);
+      for (int64_t r0 = n0; r0 < n1; r0 += kBP) {
+        for (int i = threadIdx.x; i < kBP * CMAX; i += blockDim.x) {
+          const int r = i / CMAX, c = i % CMAX;
+          dls[i] = (c < C && r0 + r < n1) ? __ldg(P.b.dlogits + (r0 + r) * C + c) : 0.f;
+        }
+        __syncthreads();  // dlogits staged; the previous tile's rows are done with dtile
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          const int q4 = threadIdx.x + h * (kBP * 32);  // float4 column of 2d / 4 = 512
+          float4 wv[CMAX];
+#pragma unroll
+          for (int c = 0; c < CMAX; ++c)
+            wv[c] = c < C ? __ldg(reinterpret_cast<const float4*>(We + c * F) + q4)
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int r = 0; r < kBP; ++r) {
+            float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int c4 = 0; c4 < CMAX / 4; ++c4) {
+              const float4 g4 = reinterpret_cast<const float4*>(dls + r * CMAX)[c4];
+              const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+              for (int qq = 0; qq < 4; ++qq) {
+                const int c = 4 * c4 + qq;
+                if (c < C) {
+                  t.x = fmaf(gv[qq], wv[c].x, t.x);
+                  t.y = fmaf(gv[qq], wv[c].y, t.y);
+                  t.z = fmaf(gv[qq], wv[c].z, t.z);
+                  t.w = fmaf(gv[qq], wv[c].w, t.w);
+                }
+              }
+            }
+            reinterpret_cast<float4*>(dtile + r * 2 * d)[q4] = t;
+          }
+        }
+        __syncthreads();  // the tile's dphi rows are complete
+        const int64_t n = r0 + warp;
+        float w[32];
+        // a row past the block's range has x-hat = 0 and dphi = 0: it adds nothing
+        bwd_core<L, FUSED, true>(P, tb, n, e, n < n1, g, lam, S, slot, bmask, poff, w);
+      }
+    }
+  }
+  if (!(FUSED && L == 10 && P.d_tile)) {
+    const int64_t units = (a.n + BS::VPW - 1) / BS::VPW;
+    const int64_t nw = (int64_t)P.bpe * kBP, q = (int64_t)sb * kBP + warp;
+    const int64_t u0 = units * q / nw, u1 = units * (q + 1) / nw;
+    for (int64_t u = u0; u < u1; ++u) {
+      const int64_t n = u * BS::VPW + g;
+      const bool valid = n < a.n;
+      float w[32];
+      // An invalid sample contributes exactly zero: x-hat = 0 gives h = 0,
+      // and its upstream gradient is read as 0 (dphi) or dlogits = 0.
+      bwd_core<L, FUSED, true>(P, tb, n, e, valid, g, lam, S, slot, bmask, poff, w);
+    }
   }
   // Sum the warp's sample groups (lanes with equal lam) into lanes of group 0,
   // then the block's warps in order, and write the block's row.
@@ -511,7 +579,7 @@ __global__ void __launch_bounds__(kBW * 32, kBwdInputMinBlocks) k_bwd_input(cons
       uint32_t poff[16];
       load_tables<L>(a, e, lam, bmask, poff);
       float w[32];
-      const BwdTabs tb{nullptr, nullptr, 0u};
+      const BwdTabs tb{nullptr, nullptr, 0u, 0u};
       bwd_core<L, FUSED, false>(P, tb, n, e, valid, g, lam, S, slot, bmask, poff, w);
 #pragma unroll
       for (int j = 0; j < 32; ++j) dx[j] += w[j];
@@ -738,8 +806,11 @@ cudaError_t run_bwd(const BwdLaunch& P0, int64_t num_partials, cudaStream_t s) {
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
       optin = 0;
-    P.w_smem = FUSED && smem_p + wbytes <= (size_t)optin;
-    if (P.w_smem) smem_p += wbytes;
+    const size_t tbytes = sizeof(float) * (size_t)kBP * (2 * ((size_t)1 << L) + CMAX);
+    P.d_tile = FUSED && L == 10 && smem_p + tbytes <= (size_t)optin;
+    P.w_smem = FUSED && !P.d_tile && smem_p + wbytes <= (size_t)optin;
+    if (P.d_tile) smem_p += tbytes;
+    else if (P.w_smem) smem_p += wbytes;
     err = cudaFuncSetAttribute(k_bwd_params<L, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem_p);
     if (err != cudaSuccess) return err;
