@@ -22,12 +22,15 @@ Reported:
   fwht_sweep   config 2: the standalone transform over 1 GiB batches, d = 2^10..2^20
   uneven_batch config 4: 10000 vectors of mixed d, E and kernel in one persistent
                graph-launched kernel vs one launch per (d, E, kernel) class
-  configs01    config 0 (256-row latency check) and config 1 (60000 rows, E=8,
-               RBF and Matern features and fused logits)
-  cpu_baseline the FP64 oracle on a bounded sample of the same workload
+  configs01    config 0 (256-row latency check), config 1 (60000 rows, E=8,
+               RBF and Matern features and fused logits) and the headline at
+               a power-of-2 batch (N = 2^16)
+  feature_sweep the batched feature kernels at d = 2^5..2^15
+  cpu_baseline the FP64 oracle on a bounded sample of the same workload, one
+               spawned process per host core (the single-core figure inside)
 
---impl reference times the oracle itself (CPU) on the same workload, as the
-reference arm.
+--impl reference times the oracle itself (CPU, every host core) on the same
+workload, as the reference arm.
 """
 
 import argparse
@@ -67,6 +70,15 @@ def parse():
     p.add_argument("--uneven-count", type=int, default=10000,
                    help="vectors in the config-4 leg (smaller values are for profiling captures)")
     return p.parse_args()
+
+
+def fp32_peak_tflops(dev, mhz=2070.0):
+    """SMs x 128 FP32 lanes x 2 (an FMA is two operations) x the maximum SM
+    clock (2070 MHz on this GPU, the clock every bench run records)."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
 
 
 def measured_peaks():
@@ -180,6 +192,52 @@ class ClockSampler:
                 "region_ms": 1e3 * (t1 - t0)}
 
 
+_WORKER_TABLES = None
+
+
+def _oracle_init(T):
+    global _WORKER_TABLES
+    _WORKER_TABLES = T
+
+
+def _oracle_shard(x):
+    """Worker of the all-core CPU runs: the oracle's features for one shard of
+    rows, with the tables the pool was started with (a checksum comes back,
+    not the features)."""
+    from oracle import fastfood as ff
+
+    return float(ff.features(x, _WORKER_TABLES).sum())
+
+
+def oracle_pool(T):
+    """One spawned process per host core, each holding the tables."""
+    import multiprocessing as mp
+
+    cores = os.cpu_count() or 1
+    return mp.get_context("spawn").Pool(cores, initializer=_oracle_init, initargs=(T,)), cores
+
+
+def cpu_baseline_all_cores(rows_per_core=CPU_SAMPLE_ROWS // 2):
+    """The same oracle, unchanged, run on every host core at once, each process
+    on its own shard of rows; the pool is started and warmed up before the
+    timed map."""
+    import workloads as wl
+    from oracle import fastfood as ff
+
+    T = ff.plan_tables(D, E, ff.RBF, SIGMA, seed=SEED)
+    pool, cores = oracle_pool(T)
+    x = wl.mnist_like(rows_per_core * cores, IN_DIM, seed=SEED).astype(np.float64)
+    shards = [x[i * rows_per_core:(i + 1) * rows_per_core] for i in range(cores)]
+    with pool:
+        pool.map(_oracle_shard, [s[:2] for s in shards])  # start-up and imports
+        t0 = time.perf_counter()
+        pool.map(_oracle_shard, shards)
+        dt = time.perf_counter() - t0
+    return {"value": rows_per_core * cores * F / dt, "unit": "features/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{rows_per_core * cores} rows ({rows_per_core} per process), float64 numpy, {dt:.1f} s"}
+
+
 def cpu_baseline(rows=CPU_SAMPLE_ROWS):
     """The FP64 oracle (as it stands, single thread) on `rows` rows of the workload."""
     import workloads as wl
@@ -202,22 +260,25 @@ def reference_arm(args):
     from oracle import fastfood as ff
 
     T = ff.plan_tables(D, E, ff.RBF, SIGMA, seed=SEED)
-    rows = 256
+    pool, cores = oracle_pool(T)
+    rows = 32 * cores  # per step: 32 rows on each host core
     x = wl.mnist_like(rows, IN_DIM, seed=SEED).astype(np.float64)
-    for _ in range(args.warmup):
-        ff.features(x[:16], T)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        ff.features(x, T)
-    dt = time.perf_counter() - t0
+    shards = [x[i * 32:(i + 1) * 32] for i in range(cores)]
+    with pool:
+        for _ in range(max(1, args.warmup)):
+            pool.map(_oracle_shard, shards)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pool.map(_oracle_shard, shards)
+        dt = time.perf_counter() - t0
     v = rows * F * args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "features/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(WORKLOAD, reference_step_rows=rows),
-            "cpu_baseline": {"value": v, "unit": "features/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{rows} rows per step, float64 numpy oracle"},
+            "cpu_baseline": {"value": v, "unit": "features/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{rows} rows per step (32 per host core), float64 numpy oracle"},
             "e2e": {"value": v, "unit": "features/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -287,7 +348,8 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
                 "kernel": "k_feat_warp<10,0>", "bytes_per_launch": nb * bytes_per_row,
-                "traffic": ncu_traffic("k_feat_warp<10,0>")}
+                "traffic": ncu_traffic("k_feat_warp<10,0>"),
+                "frac_of_nominal_7900_gbs": achieved / 7900.0}
     # Context for the write-dominated kernel: what a plain store stream reaches
     # on this GPU (torch's fill of the same output buffer, no reads), outside
     # the timed region.
@@ -337,7 +399,12 @@ def main():
             line["configs01"] = configs01_leg(mck, dev, stream, args)
     del phi
     if rank == 0 and world == 1 and not args.no_extras:
-        line["cpu_baseline"] = cpu_baseline()
+        one = cpu_baseline()
+        try:
+            line["cpu_baseline"] = cpu_baseline_all_cores()
+            line["cpu_baseline"]["single_core"] = one
+        except Exception as exc:  # a host without process spawning: one core only
+            line["cpu_baseline"] = dict(one, all_cores_error=f"{type(exc).__name__}: {exc}"[:160])
     elif rank == 0:
         line["cpu_baseline"] = None
     if rank == 0:
@@ -399,9 +466,16 @@ def fused_logits_leg(mck, plan, x, dev, stream, args):
     e.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(e) / steps
-    # FP32 FMAs: features' transforms are not counted; the contraction is C*2Ed per row.
+    # Algorithmic FP32 operations per row: the contraction (2 C 2Ed), the two
+    # transforms (2 E d log2 d add/sub) and the G and Cs products (2 E d);
+    # sin/cos not counted. Peak: SMs x 128 FP32 lanes x 2 (FMA) x SM clock.
+    ops = 2 * C * F + 2 * E * D * int(np.log2(D)) + 2 * E * D
+    tflops = n * ops / (ms / 1e3) / 1e12
+    peak_t = fp32_peak_tflops(dev)
     return {"rows": n, "samples_per_s": n / (ms / 1e3), "features_per_s": n * F / (ms / 1e3),
-            "ms_per_call": ms, "num_classes": C, "gpu_launches_per_call": 1}
+            "ms_per_call": ms, "num_classes": C, "gpu_launches_per_call": 1,
+            "alu": {"ops_per_row": ops, "achieved_tflops": tflops, "peak_tflops": peak_t,
+                    "frac": tflops / peak_t, "bound": "alu (FP32)"}}
 
 
 def fwht_sweep_leg(mck, dev, stream, args):
@@ -523,6 +597,17 @@ def configs01_leg(mck, dev, stream, args):
                                   "ms_fused_logits": ml, "logit_rows_per_s": N / (ml / 1e3)}
         pl.close()
     del f1, x1
+    # the headline at a power-of-2 batch (N = 2^16)
+    n2 = 1 << 16
+    x2 = torch.from_numpy(wl.mnist_like(n2, IN_DIM, seed=SEED)).to(dev)
+    f2 = torch.empty((n2, F), device=dev)
+    p2 = mck.Plan(D, E, "rbf", SIGMA, SEED)
+    ms = timed(lambda: mck.features(p2, x2, out=f2), max(3, args.steps // 5))
+    gbs = n2 * (IN_DIM * 4 + F * 4) / (ms / 1e3) / 1e9
+    out["headline_pow2"] = {"rows": n2, "E": E, "ms_features": ms, "features_per_s": n2 * F / (ms / 1e3),
+                            "gbs": gbs, "frac_of_measured_hbm": gbs / peak}
+    p2.close()
+    del f2, x2
     return out
 
 
@@ -712,7 +797,16 @@ def train_step_leg(mck, dev, stream, args):
     dmax = max(float((model.W.grad - Wp.grad).abs().max() / Wp.grad.abs().max()),
                float((model.G.grad - G.grad).abs().max() / G.grad.abs().max()))
     plan.close()
+    # ALU view of the fused step: 3 contractions (forward logits, dphi, dW: 2 C
+    # 2Ed each) and 6 transforms (2 forward, 2 recomputed, 2 adjoint: E d
+    # log2 d each) per row
+    ops = 3 * 2 * C * F + 6 * E * D * int(np.log2(D))
+    best = graph.get("ms_fused_graph", tf)
+    alu = {"ops_per_row": ops, "achieved_tflops": n * ops / (best / 1e3) / 1e12,
+           "peak_tflops": fp32_peak_tflops(dev)}
+    alu["frac"] = alu["achieved_tflops"] / alu["peak_tflops"]
     return {"batch": n, "ms_fused": tf, "ms_plain": tp, "speedup_vs_plain": tp / tf, **graph,
+            "alu_fused": alu,
             "grad_rel_diff_fused_vs_plain": dmax,
             "plain": "mck_features + torch matmul + torch cross_entropy + mck_features_backward"}
 
