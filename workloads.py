@@ -38,6 +38,14 @@ def labels(n, num_classes=10, seed=42):
     return _rng(seed).integers(0, num_classes, size=n, dtype=np.int32)
 
 
+def teacher_labels(x, num_classes=10, seed=42):
+    """Labels a classifier can learn: argmax of a fixed random linear map of
+    the centred inputs (entries of the map N(0,1)), as int32."""
+    g = _rng(seed)
+    V = g.standard_normal((x.shape[1], num_classes))
+    return np.argmax((x - x.mean(axis=0)) @ V, axis=1).astype(np.int32)
+
+
 def logit_weights(num_classes, num_features, seed=42, std=0.01):
     """W (C, F) float32 ~ N(0, std^2) and b = 0 (C,) float32."""
     W = (_rng(seed).standard_normal((num_classes, num_features), dtype=np.float32)
