@@ -50,9 +50,8 @@ def tune_grain(group, x, phi, grains=DEFAULT_GRAINS, reps=5, cache=None):
     """
     cache = cache if cache is not None else os.environ.get("MCK_TUNE_CACHE")
     key = signature(group)
-    if cache and os.path.exists(cache):
-        with open(cache) as f:
-            entry = json.load(f).get(key)
+    if cache:
+        entry = _read_cache(cache).get(key)
         if entry:
             group.set_grain(entry["grain"])
             return entry["grain"], {int(k): v for k, v in entry["ms"].items()}
@@ -63,11 +62,22 @@ def tune_grain(group, x, phi, grains=DEFAULT_GRAINS, reps=5, cache=None):
     best = min(times, key=times.get)
     group.set_grain(best)
     if cache:
-        data = {}
-        if os.path.exists(cache):
-            with open(cache) as f:
-                data = json.load(f)
+        data = _read_cache(cache)
         data[key] = {"grain": best, "ms": {str(k): v for k, v in times.items()}}
-        with open(cache, "w") as f:
+        # write-then-rename: several processes sharing the file (one per GPU)
+        # never see a half-written cache
+        tmp = f"{cache}.{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
             json.dump(data, f, indent=1)
+        os.replace(tmp, cache)
     return best, times
+
+
+def _read_cache(path):
+    """The cache's entries, or none if the file is missing or unreadable."""
+    try:
+        with open(path) as f:
+            data = json.load(f)
+        return data if isinstance(data, dict) else {}
+    except (OSError, ValueError):
+        return {}
