@@ -523,34 +523,40 @@ def fwht_sweep_leg(mck, dev, stream, args):
         out.append({"d": d, "batch": n, "ms": ms, "gbs": gbs, "frac_of_measured_hbm": gbs / peak,
                     "passes": 1 if L <= 17 else 2, "max_err_rel_sqrt_d_rms": rel,
                     "err_rows": rows})
-    # Tensor-core Kronecker-H16 forms at d = 1024 (16-bit operands, FP32 accumulation).
+    # Tensor-core Kronecker-H16 forms (16-bit operands, FP32 accumulation) at
+    # every d of the sweep: the tensor cores on each 1024-float block, FP32
+    # column passes for the index bits above 10 when d > 1024.
     tc = []
-    d, n = 1024, total // 1024
-    rows = (1 << 22) // d
-    xin = host[: rows * d].reshape(rows, d).astype(np.float64)
-    ref = ff.fwht(xin)
-    for prec in ("bf16", "fp16", "bf16_split", "fp16_split"):
-        work.copy_(x0)
-        mck.fwht_(work.view(n, d), prec)
-        torch.cuda.synchronize()
-        got = work[: rows * d].view(rows, d).cpu().numpy().astype(np.float64)
-        rel = float(np.abs(got - ref).max() / (np.sqrt(d) * np.sqrt((xin ** 2).mean())))
-        times = []
-        for i in range(args.warmup + max(3, args.steps // 4)):
+    for L in range(10, 21):
+        d = 1 << L
+        n = total // d
+        rows = min(n, max(1, (1 << 22) // d))
+        xin = host[: rows * d].reshape(rows, d).astype(np.float64)
+        ref = ff.fwht(xin)
+        scale = np.sqrt(d) * np.sqrt((xin ** 2).mean())
+        for prec in ("bf16", "fp16", "bf16_split", "fp16_split"):
             work.copy_(x0)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
             mck.fwht_(work.view(n, d), prec)
-            b.record(stream)
             torch.cuda.synchronize()
-            if i >= args.warmup:
-                times.append(a.elapsed_time(b))
-        ms = statistics.mean(times)
-        gbs = 8.0 * total / (ms / 1e3) / 1e9
-        tc.append({"d": d, "prec": prec, "ms": ms, "gbs": gbs, "frac_of_measured_hbm": gbs / peak,
-                   "max_err_rel_sqrt_d_rms": rel})
+            got = work[: rows * d].view(rows, d).cpu().numpy().astype(np.float64)
+            rel = float(np.abs(got - ref).max() / scale)
+            times = []
+            for i in range(args.warmup + 3):
+                work.copy_(x0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                mck.fwht_(work.view(n, d), prec)
+                b.record(stream)
+                torch.cuda.synchronize()
+                if i >= args.warmup:
+                    times.append(a.elapsed_time(b))
+            ms = statistics.mean(times)
+            gbs = 8.0 * total / (ms / 1e3) / 1e9
+            tc.append({"d": d, "prec": prec, "ms": ms, "gbs": gbs,
+                       "frac_of_measured_hbm": gbs / peak, "max_err_rel_sqrt_d_rms": rel,
+                       "passes": 1 if L <= 10 else (2 if L <= 15 else 3)})
     del work, x0
-    return {"dtype": "f32", "elements_per_d": total, "sizes": out, "tensor_core_d1024": tc}
+    return {"dtype": "f32", "elements_per_d": total, "sizes": out, "tensor_core": tc}
 
 
 def configs01_leg(mck, dev, stream, args):

@@ -117,13 +117,16 @@ mck_status_t mck_plan_tables(mck_plan_t plan, uint32_t* B_bits, uint32_t* perm, 
  *   x     device, n x d float32, contiguous, 16-byte aligned when d >= 4
  *   n     number of vectors (>= 0)
  *   d     power of two, 1 <= d <= 2^20
- *   prec  MCK_FP32: float32 butterflies, any d; d <= 2^15 runs one pass over
- *         HBM, larger d two.
+ *   prec  MCK_FP32: float32 butterflies, any d; d <= 2^17 runs one pass over
+ *         HBM (2^16 and 2^17 on thread-block clusters), larger d two.
  *         MCK_BF16 / MCK_FP16 / *_SPLIT: the Kronecker factorisation
  *         H_16 (x) H_16 (x) H_{d/256} on tensor cores (16-bit operands, the
  *         +-1 factor exact, FP32 accumulation; *_SPLIT rounds each operand
- *         as hi + lo to recover ~16 more bits); d in {256, 512, 1024} and
- *         n * d a multiple of 1024 (MCK_EUNSUPPORTED / MCK_EINVAL otherwise). */
+ *         as hi + lo to recover ~16 more bits) for d in {256, 512, 1024};
+ *         for 1024 < d <= 2^20, H_d = H_{d/1024} (x) H_1024 with the tensor
+ *         cores on every 1024-float block and FP32 column passes for the
+ *         index bits above 10. Needs 256 <= d and n * d a multiple of 1024
+ *         (MCK_EUNSUPPORTED / MCK_EINVAL otherwise). */
 mck_status_t mck_fwht(float* x, int64_t n, int64_t d, int32_t prec, mck_stream_t stream);
 
 /* phi = features of n samples (Eq. etn:mckernel, Eq. etn:mcfeatures).

@@ -340,7 +340,7 @@ mck_status_t mck_fwht(float* x, int64_t n, int64_t d, int32_t prec, mck_stream_t
   if (prec < MCK_FP32 || prec > MCK_FP16_SPLIT) return fail(MCK_EUNSUPPORTED, "unknown precision");
   if (!is_pow2(d)) return fail(MCK_EINVAL, "d must be a power of two");
   if (prec != MCK_FP32 && !fwht_mma_supported(log2i(d)))
-    return fail(MCK_EUNSUPPORTED, "the tensor-core transform supports d = 256, 512, 1024");
+    return fail(MCK_EUNSUPPORTED, "the tensor-core transform supports 256 <= d <= 2^20");
   if (prec != MCK_FP32 && ((n * d) & 1023))
     return fail(MCK_EINVAL, "the tensor-core transform needs n * d to be a multiple of 1024");
   if (d > ((int64_t)1 << MCK_MAX_LOG2_D_FWHT)) return fail(MCK_EUNSUPPORTED, "d must be <= 2^20");

@@ -311,6 +311,18 @@ cudaError_t run_cluster(float* x, int64_t n, cudaStream_t s) {
 
 }  // namespace
 
+cudaError_t launch_fwht_high_bits(float* x, int64_t n, int L, int num_sms, cudaStream_t s) {
+  if (n == 0 || L <= 15) return cudaSuccess;
+  // bits 15..L-1 at stride 2^15
+  switch (L) {
+    case 16: return run_columns<2>(x, n, num_sms, s);
+    case 17: return run_columns<4>(x, n, num_sms, s);
+    case 18: return run_columns<8>(x, n, num_sms, s);
+    case 19: return run_columns<16>(x, n, num_sms, s);
+    default: return run_columns<32>(x, n, num_sms, s);
+  }
+}
+
 cudaError_t launch_fwht(float* x, int64_t n, int L, int num_sms, cudaStream_t s) {
   if (n == 0 || L == 0) return cudaSuccess;
   switch (L) {

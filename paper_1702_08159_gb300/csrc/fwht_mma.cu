@@ -19,7 +19,10 @@
 // multiplied (two MMAs into one FP32 accumulator), which recovers ~16 more
 // bits of the input; the +-1 operand is exact either way.
 //
-// d = 256, 512, 1024 (one or more vectors per warp chunk).
+// d = 256, 512, 1024: one or more vectors per warp chunk. 2^11 <= d <= 2^15:
+// a block of d/1024 warps per vector, the index bits above 10 in FP32 after a
+// shared-memory exchange. Larger d: that on every 2^15 block, then FP32
+// column passes.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -122,14 +125,10 @@ __device__ __forceinline__ void times_h16(const uint32_t (&hi)[4], const uint32_
 __device__ __forceinline__ int frag_row(int r, int g) { return g + 8 * (r & 1); }
 __device__ __forceinline__ int frag_col(int r, int t) { return 2 * t + 8 * (r >> 1); }
 
-template <int L, int PREC, bool SPLIT>
-__global__ void __launch_bounds__(kMmaWarps * 32) k_fwht_mma(float* __restrict__ x,
-                                                             int64_t chunks) {
-  const int lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  // B operand of H16 for n-halves 0 and 1: H[k][n] = (-1)^popcount(k & n),
-  // k = 2t, 2t+1 (register 0) and 2t+8, 2t+9 (register 1), n = g (+8).
-  uint32_t hb[4];
+// B operand of H16 for n-halves 0 and 1: H[k][n] = (-1)^popcount(k & n),
+// k = 2t, 2t+1 (register 0) and 2t+8, 2t+9 (register 1), n = g (+8).
+template <int PREC>
+__device__ __forceinline__ void h16_operand(int g, int t, uint32_t (&hb)[4]) {
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
     const int n = g + 8 * half;
@@ -141,64 +140,87 @@ __global__ void __launch_bounds__(kMmaWarps * 32) k_fwht_mma(float* __restrict__
       hb[2 * half + r] = pack16<PREC>(e0, e1);
     }
   }
+}
+
+// One warp transforms index bits 0..L-1 (L <= 10) of its 1024-float chunk
+// held in v in fragment order: two H16 digits on the tensor cores, then bits
+// 8 and 9 as FP32 butterflies. On return tile `tile`, fragment (row, col) of
+// v holds chunk element tile*256 + 16*col + row.
+template <int L, int PREC, bool SPLIT>
+__device__ __forceinline__ void chunk_transform(float (&v)[4][8], const uint32_t (&hb)[4]) {
+  // Stage 1: digit c (bits 0-3).
+#pragma unroll
+  for (int tile = 0; tile < 4; ++tile) {
+    uint32_t hi[4], lo[4];
+    to_operand<PREC, SPLIT>(v[tile], hi, lo);
+    times_h16<PREC, SPLIT>(hi, lo, hb, v[tile]);
+  }
+  // Stage 2: transpose each tile (16-bit, per 8 x 8 block) and apply digit r (bits 4-7).
+#pragma unroll
+  for (int tile = 0; tile < 4; ++tile) {
+    uint32_t hi[4], lo[4], hiT[4], loT[4];
+    to_operand<PREC, SPLIT>(v[tile], hi, lo);
+    hiT[0] = transpose8x8(hi[0]);
+    hiT[1] = transpose8x8(hi[2]);
+    hiT[2] = transpose8x8(hi[1]);
+    hiT[3] = transpose8x8(hi[3]);
+    if constexpr (SPLIT) {
+      loT[0] = transpose8x8(lo[0]);
+      loT[1] = transpose8x8(lo[2]);
+      loT[2] = transpose8x8(lo[1]);
+      loT[3] = transpose8x8(lo[3]);
+    }
+    times_h16<PREC, SPLIT>(hiT, loT, hb, v[tile]);
+  }
+  // Index bits 8 and 9 (which tile): FP32 butterflies within each vector.
+  if constexpr (L >= 9) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float a0 = v[0][i], a1 = v[1][i], a2 = v[2][i], a3 = v[3][i];
+      v[0][i] = a0 + a1;
+      v[1][i] = a0 - a1;
+      v[2][i] = a2 + a3;
+      v[3][i] = a2 - a3;
+    }
+  }
+  if constexpr (L >= 10) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float a0 = v[0][i], a1 = v[1][i], a2 = v[2][i], a3 = v[3][i];
+      v[0][i] = a0 + a2;
+      v[2][i] = a0 - a2;
+      v[1][i] = a1 + a3;
+      v[3][i] = a1 - a3;
+    }
+  }
+}
+
+__device__ __forceinline__ void load_chunk(const float* __restrict__ base, int g, int t,
+                                           float (&v)[4][8]) {
+#pragma unroll
+  for (int tile = 0; tile < 4; ++tile)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float2 p = __ldcs(reinterpret_cast<const float2*>(
+          base + tile * 256 + 16 * frag_row(r, g) + frag_col(r, t)));
+      v[tile][2 * r] = p.x;
+      v[tile][2 * r + 1] = p.y;
+    }
+}
+
+template <int L, int PREC, bool SPLIT>
+__global__ void __launch_bounds__(kMmaWarps * 32) k_fwht_mma(float* __restrict__ x,
+                                                             int64_t chunks) {
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  uint32_t hb[4];
+  h16_operand<PREC>(g, t, hb);
   for (int64_t ch = (int64_t)blockIdx.x * kMmaWarps + (threadIdx.x >> 5); ch < chunks;
        ch += (int64_t)gridDim.x * kMmaWarps) {
     float* base = x + ch * 1024;
     float v[4][8];
-#pragma unroll
-    for (int tile = 0; tile < 4; ++tile)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const float2 p = __ldcs(reinterpret_cast<const float2*>(
-            base + tile * 256 + 16 * frag_row(r, g) + frag_col(r, t)));
-        v[tile][2 * r] = p.x;
-        v[tile][2 * r + 1] = p.y;
-      }
-    // Stage 1: digit c (bits 0-3).
-#pragma unroll
-    for (int tile = 0; tile < 4; ++tile) {
-      uint32_t hi[4], lo[4];
-      to_operand<PREC, SPLIT>(v[tile], hi, lo);
-      times_h16<PREC, SPLIT>(hi, lo, hb, v[tile]);
-    }
-    // Stage 2: transpose each tile (16-bit, per 8 x 8 block) and apply digit r (bits 4-7).
-#pragma unroll
-    for (int tile = 0; tile < 4; ++tile) {
-      uint32_t hi[4], lo[4], hiT[4], loT[4];
-      to_operand<PREC, SPLIT>(v[tile], hi, lo);
-      hiT[0] = transpose8x8(hi[0]);
-      hiT[1] = transpose8x8(hi[2]);
-      hiT[2] = transpose8x8(hi[1]);
-      hiT[3] = transpose8x8(hi[3]);
-      if constexpr (SPLIT) {
-        loT[0] = transpose8x8(lo[0]);
-        loT[1] = transpose8x8(lo[2]);
-        loT[2] = transpose8x8(lo[1]);
-        loT[3] = transpose8x8(lo[3]);
-      }
-      times_h16<PREC, SPLIT>(hiT, loT, hb, v[tile]);
-    }
-    // Index bits 8 and 9 (which tile): FP32 butterflies within each vector.
-    if constexpr (L >= 9) {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const float a0 = v[0][i], a1 = v[1][i], a2 = v[2][i], a3 = v[3][i];
-        v[0][i] = a0 + a1;
-        v[1][i] = a0 - a1;
-        v[2][i] = a2 + a3;
-        v[3][i] = a2 - a3;
-      }
-    }
-    if constexpr (L >= 10) {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const float a0 = v[0][i], a1 = v[1][i], a2 = v[2][i], a3 = v[3][i];
-        v[0][i] = a0 + a2;
-        v[2][i] = a0 - a2;
-        v[1][i] = a1 + a3;
-        v[3][i] = a1 - a3;
-      }
-    }
+    load_chunk(base, g, t, v);
+    chunk_transform<L, PREC, SPLIT>(v, hb);
     // The tile now holds E = Y^T (Y = H16 X H16): fragment (row, col) of E is
     // element 16*col + row of the chunk tile.
 #pragma unroll
@@ -209,6 +231,61 @@ __global__ void __launch_bounds__(kMmaWarps * 32) k_fwht_mma(float* __restrict__
         __stcs(base + tile * 256 + 16 * col + row, v[tile][2 * r]);
         __stcs(base + tile * 256 + 16 * (col + 1) + row, v[tile][2 * r + 1]);
       }
+  }
+}
+
+// One pass for 2^11 <= d <= 2^15: a block of W = d/1024 warps per vector.
+// Warp w transforms chunk w (index bits 0..9) on the tensor cores and leaves
+// it in shared memory (word i at i + 8 floor(i/32): the fragment stores fall
+// on 32 distinct banks); after a barrier thread j takes columns c = j,
+// j + 32W, ... (32/W of them) with their W values at stride 1024 and applies
+// H_W over index bits 10..L-1 in FP32 registers on the way out to HBM.
+__host__ __device__ __forceinline__ constexpr int mpad(int i) { return i + 8 * (i >> 5); }
+
+template <int L, int PREC, bool SPLIT>
+__global__ void __launch_bounds__(1 << (L - 5)) k_fwht_mma_cta(float* __restrict__ x, int64_t n) {
+  constexpr int W = 1 << (L - 10), NT = 32 * W, CPT = 32 / W;
+  extern __shared__ float4 sm4[];
+  float* sm = reinterpret_cast<float*>(sm4);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  uint32_t hb[4];
+  h16_operand<PREC>(g, t, hb);
+  for (int64_t vec = blockIdx.x; vec < n; vec += gridDim.x) {
+    float* row = x + (vec << L);
+    {
+      float v[4][8];
+      load_chunk(row + warp * 1024, g, t, v);
+      chunk_transform<10, PREC, SPLIT>(v, hb);
+#pragma unroll
+      for (int tile = 0; tile < 4; ++tile)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int i = warp * 1024 + tile * 256 + 16 * frag_col(r, t) + frag_row(r, g);
+          sm[mpad(i)] = v[tile][2 * r];
+          sm[mpad(i + 16)] = v[tile][2 * r + 1];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      const int c = threadIdx.x + NT * j;
+      float u[W];
+#pragma unroll
+      for (int i = 0; i < W; ++i) u[i] = sm[mpad(c + 1024 * i)];
+#pragma unroll
+      for (int h = 1; h < W; h <<= 1)
+#pragma unroll
+        for (int i = 0; i < W; ++i)
+          if (!(i & h)) {
+            const float a = u[i], b = u[i | h];
+            u[i] = a + b;
+            u[i | h] = a - b;
+          }
+#pragma unroll
+      for (int i = 0; i < W; ++i) __stcs(row + c + 1024 * i, u[i]);
+    }
+    __syncthreads();  // the slice is read before the next vector overwrites it
   }
 }
 
@@ -226,6 +303,32 @@ cudaError_t run(float* x, int64_t chunks, int num_sms, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int L, int PREC, bool SPLIT>
+cudaError_t run_cta(float* x, int64_t n, int num_sms, cudaStream_t s) {
+  auto kern = k_fwht_mma_cta<L, PREC, SPLIT>;
+  const size_t smem = sizeof(float) * (size_t)mpad(1 << L);
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 1 << (L - 5), smem) != cudaSuccess)
+    occ = 1;
+  occ = std::max(occ, 1);
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)num_sms * occ));
+  kern<<<grid, 1 << (L - 5), smem, s>>>(x, n);
+  return cudaGetLastError();
+}
+
+template <int L>
+cudaError_t run_cta_prec(float* x, int64_t n, int prec, int num_sms, cudaStream_t s) {
+  switch (prec) {
+    case MCK_BF16: return run_cta<L, MCK_BF16, false>(x, n, num_sms, s);
+    case MCK_FP16: return run_cta<L, MCK_FP16, false>(x, n, num_sms, s);
+    case MCK_BF16_SPLIT: return run_cta<L, MCK_BF16, true>(x, n, num_sms, s);
+    case MCK_FP16_SPLIT: return run_cta<L, MCK_FP16, true>(x, n, num_sms, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int L>
 cudaError_t run_prec(float* x, int64_t chunks, int prec, int num_sms, cudaStream_t s) {
   switch (prec) {
@@ -239,7 +342,7 @@ cudaError_t run_prec(float* x, int64_t chunks, int prec, int num_sms, cudaStream
 
 }  // namespace
 
-bool fwht_mma_supported(int L) { return L >= 8 && L <= 10; }
+bool fwht_mma_supported(int L) { return L >= 8 && L <= 20; }
 
 cudaError_t launch_fwht_mma(float* x, int64_t n, int L, int prec, int num_sms, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
@@ -249,9 +352,24 @@ cudaError_t launch_fwht_mma(float* x, int64_t n, int L, int prec, int num_sms, c
   switch (L) {
     case 8: return run_prec<8>(x, chunks, prec, num_sms, s);
     case 9: return run_prec<9>(x, chunks, prec, num_sms, s);
-    case 10: return run_prec<10>(x, chunks, prec, num_sms, s);
-    default: return cudaErrorInvalidValue;
+    default: break;
   }
+  if (L == 10) return run_prec<10>(x, chunks, prec, num_sms, s);
+  // 2^11 <= d <= 2^15: one pass, a block of d/1024 warps per vector (the
+  // tensor cores on each 1024-float block, FP32 for index bits 10..L-1).
+  switch (L) {
+    case 11: return run_cta_prec<11>(x, n, prec, num_sms, s);
+    case 12: return run_cta_prec<12>(x, n, prec, num_sms, s);
+    case 13: return run_cta_prec<13>(x, n, prec, num_sms, s);
+    case 14: return run_cta_prec<14>(x, n, prec, num_sms, s);
+    case 15: return run_cta_prec<15>(x, n, prec, num_sms, s);
+    default: break;
+  }
+  // d > 2^15: that pass on every 2^15 block, then an FP32 column pass over
+  // index bits 15..L-1 (H_d = H_{d/2^15} (x) H_{2^15}).
+  cudaError_t err = run_cta_prec<15>(x, n << (L - 15), prec, num_sms, s);
+  if (err != cudaSuccess) return err;
+  return launch_fwht_high_bits(x, n, L, num_sms, s);
 }
 
 }  // namespace mck

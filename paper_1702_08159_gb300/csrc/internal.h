@@ -44,6 +44,8 @@ mck_status_t build_tables(mck_plan_s* p, cudaStream_t s);
 
 // ---- fwht.cu -------------------------------------------------------------
 cudaError_t launch_fwht(float* x, int64_t n, int L, int num_sms, cudaStream_t s);
+// H over index bits 15..L-1 of n vectors of 2^L (FP32 column pass; 16 <= L <= 20).
+cudaError_t launch_fwht_high_bits(float* x, int64_t n, int L, int num_sms, cudaStream_t s);
 
 // ---- fwht_mma.cu -----------------------------------------------------------
 bool fwht_mma_supported(int L);

@@ -39,6 +39,26 @@ def test_tensor_core_transform_accuracy(mck, dev, d, prec):
 
 
 @pytest.mark.parametrize("prec", list(BOUND))
+@pytest.mark.parametrize("L,n", [(11, 3), (13, 2), (15, 1), (16, 1), (18, 1), (20, 1)])
+def test_tensor_core_large_d(mck, dev, L, n, prec):
+    # d > 1024: tensor cores on every 1024-float block, FP32 column passes above
+    d = 1 << L
+    x = wl.gaussian(n, d, seed=L)
+    t = torch.from_numpy(x).to(dev)
+    mck.fwht_(t, prec)
+    err = _rel_err(t.cpu().numpy(), x)
+    assert err <= BOUND[prec], (d, prec, err)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16_split"])
+def test_tensor_core_basis_vectors_exact_d4096(mck, dev, prec):
+    d = 4096
+    t = torch.eye(d, device=dev)
+    mck.fwht_(t, prec)
+    np.testing.assert_array_equal(t.cpu().numpy(), ff.sylvester(d))
+
+
+@pytest.mark.parametrize("prec", list(BOUND))
 def test_tensor_core_basis_vectors_exact(mck, dev, prec):
     # H e_i is a row of the Sylvester matrix: +-1 values, exact in every precision.
     d = 1024
