@@ -8,11 +8,13 @@
 //   L = 5..10   a group of 2^(L-5) lanes per vector (32/2^(L-5) vectors per
 //               warp): register phases A and B with one shared-memory layout
 //               move in between, 128-bit coalesced global loads and stores.
-//   L = 11..15  one block of 2^(L-5) threads per vector: phases A, B, C.
+//   L = 11..15  one block of 2^(L-10) warps per vector: each warp transforms
+//               a 1024-float chunk like the d = 1024 kernel, then one
+//               shared-memory exchange carries index bits 10..L-1.
 //   L = 16, 17  one pass: a thread-block cluster of 2^(L-15) blocks per
-//               vector; each block transforms a 2^15 slice, then the rank
-//               bits are transformed across the cluster through distributed
-//               shared memory on the way out to HBM.
+//               vector; each block transforms a 2^15 slice that way, then
+//               the rank bits are transformed across the cluster through
+//               distributed shared memory on the way out to HBM.
 //   L = 18..20  two passes over HBM: the L = 15 kernel on every 2^15 block
 //               (index bits 0..14), then a column pass over bits 15..L-1.
 // Every element is read and written once per pass.
@@ -111,32 +113,53 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_fwht_warp(float* __rest
   }
 }
 
-// One block per vector of 2^L (11 <= L <= 15); blocks stride over vectors.
+// One block of W = 2^(L-10) warps per vector (11 <= L <= 15). Warp w
+// transforms chunk w (index bits 0..9) exactly like the d = 1024 warp kernel,
+// leaving it in natural order in its own 1056-word slot of shared memory;
+// after one block barrier thread j takes columns c = j, j + 32W, ...
+// (32/W of them) with their W values at stride 1024 and applies H_W over
+// index bits 10..L-1 in registers on the way out to HBM (coalesced).
 template <int L>
-__global__ void __launch_bounds__(1 << (L - 5)) k_fwht_cta(float* __restrict__ x, int64_t n) {
-  using Y = Lay<L>;
+__global__ void __launch_bounds__(1 << (L - 5)) k_fwht_chunks(float* __restrict__ x, int64_t n) {
+  using Y = Lay<10>;
+  constexpr int W = 1 << (L - 10), NT = 32 * W, CPT = 32 / W;
   extern __shared__ float4 sm4[];
-  float* buf = reinterpret_cast<float*>(sm4);
-  const int lam = threadIdx.x;
+  float* sm = reinterpret_cast<float*>(sm4);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* buf = sm + warp * Y::SLOT;
   for (int64_t v = blockIdx.x; v < n; v += gridDim.x) {
-    float* row = x + v * Y::d;
-    float w[32];
-    gload_A<L>(row, lam, true, w);
-    hreg<Y::maskA()>(w);
-    // Barriers only between a store phase and the next load phase: a thread
-    // rewrites exactly the slots it read, so loads need no trailing barrier.
-    store_A<L>(buf, 0, lam, w);
+    float* row = x + (v << L);
+    {
+      float w[32];
+      gload_A<10>(row + warp * 1024, lane, true, w);
+      hreg<Y::maskA()>(w);
+      store_A<10>(buf, 0, lane, w);
+      __syncwarp();
+      load_B<10>(buf, 0, lane, w);
+      hreg<Y::maskB()>(w);
+      __syncwarp();
+      store_B<10>(buf, 0, lane, w);
+    }
     __syncthreads();
-    load_B<L>(buf, 0, lam, w);
-    hreg<Y::maskB()>(w);
-    store_B<L>(buf, 0, lam, w);
-    __syncthreads();
-    load_C<L>(buf, lam, w);
-    hreg<Y::maskC()>(w);
-    store_C<L>(buf, lam, w);
-    __syncthreads();
-    load_A<L>(buf, 0, lam, w);
-    gstore_A<L>(row, lam, w);
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      const int c = threadIdx.x + NT * j;
+      float u[W];
+#pragma unroll
+      for (int i = 0; i < W; ++i) u[i] = sm[i * Y::SLOT + pad(c)];
+#pragma unroll
+      for (int h = 1; h < W; h <<= 1)
+#pragma unroll
+        for (int i = 0; i < W; ++i)
+          if (!(i & h)) {
+            const float a = u[i], b = u[i | h];
+            u[i] = a + b;
+            u[i | h] = a - b;
+          }
+#pragma unroll
+      for (int i = 0; i < W; ++i) __stcs(row + c + 1024 * i, u[i]);
+    }
+    __syncthreads();  // the slots are read before the next vector overwrites them
   }
 }
 
@@ -171,46 +194,72 @@ __global__ void __launch_bounds__(256) k_fwht_columns(float* __restrict__ x, int
 
 // One vector of 2^(LS + log2 CS) per thread-block cluster of CS blocks
 // (single pass over HBM). Block r of the cluster loads slice r (index bits
-// 0..LS-1 local, bits LS.. = r), transforms the local bits in registers and
-// shared memory (phases A, B, C), and leaves the slice in shared memory in
-// natural order. After a cluster barrier, block r takes 1/CS of the local
-// indices, four consecutive at a time: it reads the CS slices' values there
-// through distributed shared memory (128-bit), applies H_CS (the rank bits)
-// and writes the CS results to HBM (128-bit, coalesced). A second cluster barrier keeps the slices alive until every
+// 0..LS-1 local, bits LS.. = r) and transforms the local bits as the chunked
+// block kernel does (bits 0..9 per warp, then 10..LS-1 across the chunks),
+// leaving the slice in shared memory. After a cluster barrier, block r takes
+// 1/CS of the local indices, four consecutive at a time: it reads the CS
+// slices' values there through distributed shared memory (128-bit), applies
+// H_CS (the rank bits) and writes the CS results to HBM (128-bit,
+// coalesced). A second cluster barrier keeps the slices alive until every
 // block has read them.
 template <int LS, int CS>
 __global__ void __launch_bounds__(1 << (LS - 5)) k_fwht_cluster(float* __restrict__ x, int64_t n) {
-  using Y = Lay<LS>;
-  constexpr int S = Y::d, T = Y::T, OWN = S / CS, PER4 = OWN / (4 * T);
-  static_assert(LS >= 11 && PER4 * 4 * CS == 32, "cluster slices (2 <= CS <= 8)");
+  using Y = Lay<10>;
+  constexpr int S = 1 << LS, W = 1 << (LS - 10), NT = 32 * W, CPT = 32 / W;
+  constexpr int OWN = S / CS, PER4 = OWN / (4 * NT);
+  static_assert(LS >= 11 && LS <= 15 && PER4 >= 1 && PER4 * 4 * NT * CS == S,
+                "cluster slices (2 <= CS <= 8)");
   extern __shared__ float4 sm4[];
-  float* buf = reinterpret_cast<float*>(sm4);
+  float* sm = reinterpret_cast<float*>(sm4);  // W slots of 1056 words: chunk i at i * SLOT + pad(c)
   cg::cluster_group cl = cg::this_cluster();
   const int r = (int)cl.block_rank();
-  const int lam = threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* buf = sm + warp * Y::SLOT;
   const int64_t ncl = gridDim.x / CS;
   for (int64_t v = blockIdx.x / CS; v < n; v += ncl) {
     float* row = x + v * (int64_t)(S * CS);
-    float w[32];
-    gload_A<LS>(row + (int64_t)r * S, lam, true, w);
-    hreg<Y::maskA()>(w);
-    store_A<LS>(buf, 0, lam, w);
+    // index bits 0..9: warp w transforms chunk w of the slice in registers
+    {
+      float w[32];
+      gload_A<10>(row + (int64_t)r * S + warp * 1024, lane, true, w);
+      hreg<Y::maskA()>(w);
+      store_A<10>(buf, 0, lane, w);
+      __syncwarp();
+      load_B<10>(buf, 0, lane, w);
+      hreg<Y::maskB()>(w);
+      __syncwarp();
+      store_B<10>(buf, 0, lane, w);
+    }
     __syncthreads();
-    load_B<LS>(buf, 0, lam, w);
-    hreg<Y::maskB()>(w);
-    store_B<LS>(buf, 0, lam, w);
-    __syncthreads();
-    load_C<LS>(buf, lam, w);
-    hreg<Y::maskC()>(w);
-    store_C<LS>(buf, lam, w);
+    // index bits 10..LS-1: across the slice's chunks, in place
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      const int c = threadIdx.x + NT * j;
+      float u[W];
+#pragma unroll
+      for (int i = 0; i < W; ++i) u[i] = sm[i * Y::SLOT + pad(c)];
+#pragma unroll
+      for (int h = 1; h < W; h <<= 1)
+#pragma unroll
+        for (int i = 0; i < W; ++i)
+          if (!(i & h)) {
+            const float a = u[i], b = u[i | h];
+            u[i] = a + b;
+            u[i | h] = a - b;
+          }
+#pragma unroll
+      for (int i = 0; i < W; ++i) sm[i * Y::SLOT + pad(c)] = u[i];
+    }
     cl.sync();  // every slice is transformed over its local bits
+    // rank bits: block r takes local indices [r OWN, (r+1) OWN), four at a time
 #pragma unroll
     for (int q = 0; q < PER4; ++q) {
-      const int i = r * OWN + 4 * (q * T + lam);  // four consecutive local indices
+      const int i = r * OWN + 4 * (q * NT + (int)threadIdx.x);
+      const int at = (i >> 10) * Y::SLOT + pad(i & 1023);  // 4 consecutive words
       float4 u[CS];
 #pragma unroll
       for (int c = 0; c < CS; ++c)
-        u[c] = *reinterpret_cast<const float4*>(cl.map_shared_rank(buf, c) + pad(i));
+        u[c] = *reinterpret_cast<const float4*>(cl.map_shared_rank(sm, c) + at);
 #pragma unroll
       for (int h = 1; h < CS; h <<= 1)
 #pragma unroll
@@ -259,13 +308,13 @@ cudaError_t run_warp(float* x, int64_t n, int num_sms, cudaStream_t s) {
 }
 
 template <int L>
-cudaError_t run_cta(float* x, int64_t n, int num_sms, cudaStream_t s) {
-  const size_t smem = sizeof(float) * Lay<L>::SLOT;
+cudaError_t run_chunks(float* x, int64_t n, int num_sms, cudaStream_t s) {
+  const size_t smem = sizeof(float) * ((size_t)Lay<10>::SLOT << (L - 10));
   cudaError_t err =
-      cudaFuncSetAttribute(k_fwht_cta<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_fwht_chunks<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  const int occ = occupancy_blocks(k_fwht_cta<L>, Lay<L>::T, smem);
-  k_fwht_cta<L><<<grid_for(n, 1, num_sms, occ), Lay<L>::T, smem, s>>>(x, n);
+  const int occ = occupancy_blocks(k_fwht_chunks<L>, 1 << (L - 5), smem);
+  k_fwht_chunks<L><<<grid_for(n, 1, num_sms, occ), 1 << (L - 5), smem, s>>>(x, n);
   return cudaGetLastError();
 }
 
@@ -279,7 +328,7 @@ cudaError_t run_columns(float* x, int64_t n, int num_sms, cudaStream_t s) {
 template <int LS, int CS>
 cudaError_t run_cluster(float* x, int64_t n, cudaStream_t s) {
   auto kern = k_fwht_cluster<LS, CS>;
-  const size_t smem = sizeof(float) * Lay<LS>::SLOT;
+  const size_t smem = sizeof(float) * ((size_t)Lay<10>::SLOT << (LS - 10));
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   if (CS > 8) {
@@ -336,11 +385,11 @@ cudaError_t launch_fwht(float* x, int64_t n, int L, int num_sms, cudaStream_t s)
     case 8: return run_warp<8>(x, n, num_sms, s);
     case 9: return run_warp<9>(x, n, num_sms, s);
     case 10: return run_warp<10>(x, n, num_sms, s);
-    case 11: return run_cta<11>(x, n, num_sms, s);
-    case 12: return run_cta<12>(x, n, num_sms, s);
-    case 13: return run_cta<13>(x, n, num_sms, s);
-    case 14: return run_cta<14>(x, n, num_sms, s);
-    case 15: return run_cta<15>(x, n, num_sms, s);
+    case 11: return run_chunks<11>(x, n, num_sms, s);
+    case 12: return run_chunks<12>(x, n, num_sms, s);
+    case 13: return run_chunks<13>(x, n, num_sms, s);
+    case 14: return run_chunks<14>(x, n, num_sms, s);
+    case 15: return run_chunks<15>(x, n, num_sms, s);
     default: break;
   }
   if (L > 20) return cudaErrorInvalidValue;
@@ -350,7 +399,7 @@ cudaError_t launch_fwht(float* x, int64_t n, int L, int num_sms, cudaStream_t s)
   if (L == 16) return run_cluster<15, 2>(x, n, s);
   if (L == 17) return run_cluster<15, 4>(x, n, s);
   const int64_t blocks = n << (L - 15);
-  cudaError_t err = run_cta<15>(x, blocks, num_sms, s);
+  cudaError_t err = run_chunks<15>(x, blocks, num_sms, s);
   if (err != cudaSuccess) return err;
   switch (L) {
     case 16: return run_columns<2>(x, n, num_sms, s);
