@@ -261,7 +261,7 @@ mck_status_t mck_plan_ex(mck_plan_t* out, int64_t d, int32_t E, int32_t kernel, 
             cudaMalloc(&p->perm, sizeof(uint32_t) * n) == cudaSuccess &&
             cudaMalloc(&p->G, sizeof(float) * n) == cudaSuccess &&
             cudaMalloc(&p->Cs, sizeof(float) * n) == cudaSuccess;
-  if (ok && p->L >= 5 && p->L <= 10) {
+  if (ok && p->L >= 5 && p->L <= 14) {
     const size_t T = (size_t)1 << (p->L - 5);
     ok = cudaMalloc(&p->permB, sizeof(uint32_t) * n) == cudaSuccess &&
          cudaMalloc(&p->GB, sizeof(float) * n) == cudaSuccess &&

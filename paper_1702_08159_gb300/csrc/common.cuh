@@ -224,4 +224,68 @@ __device__ __forceinline__ void load_C(const float* buf, int lam, float (&w)[32]
   for (int j = 0; j < 32; ++j) w[j] = p[pad(Lay<L>::kC_r(j))];
 }
 
+// ---------------------------------------------------------------------------
+// Chunked block form of the feature map for 11 <= L <= 14: a (sub-)block of
+// W = 2^(L-10) warps owns one vector-expansion; warp w owns the 1024-float
+// chunk w (elements 1024 w .. 1024 w + 1023) and transforms its index bits
+// 0..9 exactly like the d = 1024 warp kernel (layouts A and B, warp-local
+// moves through its 1056-word slot); index bits 10..L-1 are transformed
+// across the chunks by threads that own columns c of all W slots. The Pi
+// gather reads the whole vector from the slots through word offsets made at
+// plan time. Four block barriers per vector-expansion.
+// ---------------------------------------------------------------------------
+template <int L>
+struct Chunked {
+  static_assert(L >= 11 && L <= 14, "chunked block form");
+  static constexpr int W = 1 << (L - 10);                  // warps (chunks)
+  static constexpr int NT = 32 * W;                        // threads
+  static constexpr int VEC = (1024 / NT) >= 4 ? 4 : 2;     // columns per vector access
+  static constexpr int CG = 1024 / (NT * VEC);             // column groups per thread
+  static constexpr int SLOT = Lay<10>::SLOT;               // words per chunk slot
+  static constexpr int WORDS = W * SLOT;
+};
+
+template <int VEC>
+__device__ __forceinline__ void ld_vec(const float* p, float (&v)[VEC]) {
+  if constexpr (VEC == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  }
+}
+template <int VEC>
+__device__ __forceinline__ void st_vec(float* p, const float (&v)[VEC]) {
+  if constexpr (VEC == 4) *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  else *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+}
+
+// H over index bits 10..L-1 of the vector held in the W slots, in place
+// (thread tid owns column groups tid, tid + NT, ...).
+template <int L>
+__device__ __forceinline__ void chunk_columns_inplace(float* sm, int tid) {
+  using C = Chunked<L>;
+#pragma unroll
+  for (int q = 0; q < C::CG; ++q) {
+    const int c0 = C::VEC * (tid + C::NT * q);
+    float u[C::W][C::VEC];
+#pragma unroll
+    for (int i = 0; i < C::W; ++i) ld_vec<C::VEC>(sm + i * C::SLOT + pad(c0), u[i]);
+#pragma unroll
+    for (int h = 1; h < C::W; h <<= 1)
+#pragma unroll
+      for (int i = 0; i < C::W; ++i)
+        if (!(i & h))
+#pragma unroll
+          for (int v = 0; v < C::VEC; ++v) {
+            const float a = u[i][v], b = u[i | h][v];
+            u[i][v] = a + b;
+            u[i | h][v] = a - b;
+          }
+#pragma unroll
+    for (int i = 0; i < C::W; ++i) st_vec<C::VEC>(sm + i * C::SLOT + pad(c0), u[i]);
+  }
+}
+
 }  // namespace mck

@@ -26,9 +26,12 @@ struct mck_plan_s {
   // Lane-ordered copies for the warp kernels (32 <= d <= 1024), built at plan
   // time so a warp loads an expansion's tables with coalesced 128-bit loads:
   // entry (e, m, lam, q) describes element k = kB(lam, 4m+q) of layout B.
-  uint32_t* permB = nullptr;   // E x d: byte offset 4*pad(pi_e(k)) inside a vector slot
+  // Lane-ordered tables (5 <= L <= 14). L <= 10: Pi as the byte offset
+  // 4*pad(pi_e(k)) inside a vector slot. 11 <= L <= 14, per 1024-float chunk:
+  // Pi as the word offset of pi_e(k) in the chunked block layout.
+  uint32_t* permB = nullptr;   // E x d
   float* GB = nullptr;         // E x d: G_e[k]
-  uint32_t* maskA = nullptr;   // E x T: bit j set where B_e[kA(lam, j)] = -1
+  uint32_t* maskA = nullptr;   // E x d/32: bit j set where B_e[kA(lam, j)] = -1
 };
 
 namespace mck {

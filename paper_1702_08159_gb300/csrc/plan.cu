@@ -260,7 +260,46 @@ __global__ void k_plan_lane_tables(const uint32_t* __restrict__ perm, const floa
   }
 }
 
+// The same tables for the chunked block kernels (11 <= L <= 14): vector
+// element k = 1024 w + k' belongs to chunk w, and chunk w is laid out as a
+// d = 1024 vector (k' = kB10(lam, 4m + q) for entry t = (e, w, m, lam, q)).
+// Pi is stored as the word offset of pi(k) in the block's shared memory,
+// where chunk i occupies 1056 words from i * 1056 (< 2^16 for L <= 14); the
+// mask word (e, w, lam) has bit j for element 1024 w + kA10(lam, j).
+template <int L>
+__global__ void k_plan_chunk_tables(const uint32_t* __restrict__ perm, const float* __restrict__ G,
+                                    const uint32_t* __restrict__ bits, uint32_t* __restrict__ permB,
+                                    float* __restrict__ GB, uint32_t* __restrict__ maskA, int32_t E) {
+  using Y = Lay<10>;
+  constexpr int d = 1 << L;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)E * d) return;
+  const int64_t e = t / d;
+  const int r = (int)(t % d);
+  const int w = r >> 10, rr = r & 1023;
+  const int q = rr & 3, lam = (rr >> 2) & 31, m = rr >> 7;
+  const int k = 1024 * w + Y::kB(lam, 4 * m + q);
+  const int src = (int)perm[e * d + k];
+  permB[t] = (uint32_t)((src >> 10) * Y::SLOT + pad(src & 1023));
+  GB[t] = G[e * d + k];
+  if (m == 0 && q == 0) {
+    uint32_t mask = 0;
+    for (int j = 0; j < 32; ++j) {
+      const int kk = 1024 * w + Y::kA(lam, j);
+      mask |= ((bits[e * (d / 32) + (kk >> 5)] >> (kk & 31)) & 1u) << j;
+    }
+    maskA[e * (d / 32) + w * 32 + lam] = mask;
+  }
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <int L>
+void launch_chunk_tables(mck_plan_s* p, cudaStream_t s) {
+  k_plan_chunk_tables<L><<<blocks_for(p->d * p->E, 256), 256, 0, s>>>(p->perm, p->G, p->B_bits,
+                                                                      p->permB, p->GB, p->maskA,
+                                                                      p->E);
+}
 
 template <int L>
 void launch_lane_tables(mck_plan_s* p, cudaStream_t s) {
@@ -313,6 +352,10 @@ mck_status_t build_tables(mck_plan_s* p, cudaStream_t s) {
       case 8: launch_lane_tables<8>(p, s); break;
       case 9: launch_lane_tables<9>(p, s); break;
       case 10: launch_lane_tables<10>(p, s); break;
+      case 11: launch_chunk_tables<11>(p, s); break;
+      case 12: launch_chunk_tables<12>(p, s); break;
+      case 13: launch_chunk_tables<13>(p, s); break;
+      case 14: launch_chunk_tables<14>(p, s); break;
       default: break;
     }
     err = cudaGetLastError();

@@ -72,17 +72,18 @@ def test_ragged_batches(mck, dev, n):
         assert _max_err(phi, ref) <= TOL
 
 
-def test_strided_and_misaligned_rows(mck, dev):
-    plan = mck.Plan(1024, 2, "rbf", 1.0, 13)
-    base = wl.mnist_like(10, 900, seed=3)
+@pytest.mark.parametrize("d,in_dim,ld", [(1024, 784, 900), (4096, 3001, 3100), (16384, 12000, 12345)])
+def test_strided_and_misaligned_rows(mck, dev, d, in_dim, ld):
+    plan = mck.Plan(d, 2, "rbf", 1.0, 13)
+    base = (wl.mnist_like(6, ld, seed=3) * np.float32(np.sqrt(784 / in_dim))).astype(np.float32)
     t = torch.from_numpy(base).to(dev)
     ref_tab = _oracle_tables(plan)
-    # rows with leading dimension 900 > in_dim 784
-    phi = mck.features(plan, t[:, :784]).cpu().numpy()
-    assert _max_err(phi, ff.features(base[:, :784].astype(np.float64), ref_tab)) <= TOL
+    # rows with leading dimension ld > in_dim
+    phi = mck.features(plan, t[:, :in_dim]).cpu().numpy()
+    assert _max_err(phi, ff.features(base[:, :in_dim].astype(np.float64), ref_tab)) <= TOL
     # rows starting one float past a 16-byte boundary (scalar load path)
-    phi = mck.features(plan, t[:, 1:785]).cpu().numpy()
-    assert _max_err(phi, ff.features(base[:, 1:785].astype(np.float64), ref_tab)) <= TOL
+    phi = mck.features(plan, t[:, 1:in_dim + 1]).cpu().numpy()
+    assert _max_err(phi, ff.features(base[:, 1:in_dim + 1].astype(np.float64), ref_tab)) <= TOL
 
 
 def test_empty_batch(mck, dev):
