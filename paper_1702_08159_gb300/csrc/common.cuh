@@ -288,4 +288,136 @@ __device__ __forceinline__ void chunk_columns_inplace(float* sm, int tid) {
   }
 }
 
+// The whole feature map of one vector-expansion in the chunked block form.
+// Tables are the expansion's (offset by e d): Pi as shared-memory word
+// offsets and G lane-ordered per chunk (GB), or G in natural order (Gnat)
+// when the caller overrides it; the B masks per (chunk, lane); Cs natural.
+// `out` receives [cos z | sin z] (2d floats). `bar` synchronises the NT
+// threads of the (sub-)block.
+template <int L, class Bar>
+__device__ __forceinline__ void chunked_map(const float* __restrict__ xrow, int64_t in_dim,
+                                            bool vec_x, const uint32_t* __restrict__ permB,
+                                            const float* __restrict__ GB,
+                                            const float* __restrict__ Gnat,
+                                            const uint32_t* __restrict__ maskA,
+                                            const float* __restrict__ cs, float* __restrict__ out,
+                                            float* sm, int tid, Bar bar) {
+  using C = Chunked<L>;
+  using Y = Lay<10>;
+  constexpr int d = 1 << L;
+  const int warp = tid >> 5, lane = tid & 31;
+  float* slot = sm + warp * C::SLOT;
+  const uint32_t sbase = smem_addr(sm);
+  const int co = warp * 1024;
+  const uint32_t bmask = __ldg(maskA + warp * 32 + lane);
+  uint32_t poff[16];
+  float gt[32];
+  {
+    const uint4* pb = reinterpret_cast<const uint4*>(permB + co) + lane;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const uint4 v = __ldg(pb + m * 32);
+      poff[2 * m] = v.x | (v.y << 16);
+      poff[2 * m + 1] = v.z | (v.w << 16);
+    }
+    if (Gnat) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) gt[j] = __ldg(Gnat + co + Y::kB(lane, j));
+    } else {
+      const float4* gb = reinterpret_cast<const float4*>(GB + co) + lane;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const float4 v = __ldg(gb + m * 32);
+        gt[4 * m] = v.x;
+        gt[4 * m + 1] = v.y;
+        gt[4 * m + 2] = v.z;
+        gt[4 * m + 3] = v.w;
+      }
+    }
+  }
+  // u = H B x-hat: index bits 0..9 per warp, then 10..L-1 across the chunks
+  {
+    float w[32];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int k0 = co + Y::kA(lane, 4 * m);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (vec_x) {
+        if (k0 < in_dim) v = __ldg(reinterpret_cast<const float4*>(xrow + k0));
+      } else {
+        if (k0 + 0 < in_dim) v.x = __ldg(xrow + k0 + 0);
+        if (k0 + 1 < in_dim) v.y = __ldg(xrow + k0 + 1);
+        if (k0 + 2 < in_dim) v.z = __ldg(xrow + k0 + 2);
+        if (k0 + 3 < in_dim) v.w = __ldg(xrow + k0 + 3);
+      }
+      w[4 * m] = v.x;
+      w[4 * m + 1] = v.y;
+      w[4 * m + 2] = v.z;
+      w[4 * m + 3] = v.w;
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      w[j] = __int_as_float(__float_as_int(w[j]) ^ ((bmask << (31 - j)) & 0x80000000u));
+    hreg<Y::maskA()>(w);
+    store_A<10>(slot, 0, lane, w);
+    __syncwarp();
+    load_B<10>(slot, 0, lane, w);
+    hreg<Y::maskB()>(w);
+    __syncwarp();
+    store_B<10>(slot, 0, lane, w);
+  }
+  bar();
+  chunk_columns_inplace<L>(sm, tid);
+  bar();
+  // v = Pi u gathered into chunk `warp` (layout B), G, H over bits 0..9
+  float w[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j)
+    w[j] = lds32(sbase + 4u * ((j & 1) ? (poff[j >> 1] >> 16) : (poff[j >> 1] & 0xffffu)));
+  hreg_scaled<Y::maskB()>(w, gt);
+  bar();  // every warp has gathered: the slots may be rewritten
+  store_B<10>(slot, 0, lane, w);
+  __syncwarp();
+  load_A<10>(slot, 0, lane, w);
+  hreg<Y::maskA()>(w);
+  __syncwarp();
+  store_A<10>(slot, 0, lane, w);
+  bar();
+  // bits 10..L-1 of the second transform, then z = Cs h and [cos | sin]
+#pragma unroll
+  for (int q = 0; q < C::CG; ++q) {
+    const int c0 = C::VEC * (tid + C::NT * q);
+    float u[C::W][C::VEC];
+#pragma unroll
+    for (int i = 0; i < C::W; ++i) ld_vec<C::VEC>(sm + i * C::SLOT + pad(c0), u[i]);
+#pragma unroll
+    for (int h = 1; h < C::W; h <<= 1)
+#pragma unroll
+      for (int i = 0; i < C::W; ++i)
+        if (!(i & h))
+#pragma unroll
+          for (int v = 0; v < C::VEC; ++v) {
+            const float a = u[i][v], b = u[i | h][v];
+            u[i][v] = a + b;
+            u[i | h][v] = a - b;
+          }
+#pragma unroll
+    for (int i = 0; i < C::W; ++i) {
+      const int k = c0 + 1024 * i;
+      float cv[C::VEC], cz[C::VEC], sz[C::VEC];
+      ld_vec<C::VEC>(cs + k, cv);
+#pragma unroll
+      for (int v = 0; v < C::VEC; ++v) cos_sin(cv[v] * u[i][v], cz[v], sz[v]);
+      if constexpr (C::VEC == 4) {
+        __stcs(reinterpret_cast<float4*>(out + k), make_float4(cz[0], cz[1], cz[2], cz[3]));
+        __stcs(reinterpret_cast<float4*>(out + d + k), make_float4(sz[0], sz[1], sz[2], sz[3]));
+      } else {
+        __stcs(reinterpret_cast<float2*>(out + k), make_float2(cz[0], cz[1]));
+        __stcs(reinterpret_cast<float2*>(out + d + k), make_float2(sz[0], sz[1]));
+      }
+    }
+  }
+  bar();  // the slots are read before the next item rewrites them
+}
+
 }  // namespace mck

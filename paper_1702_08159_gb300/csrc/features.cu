@@ -391,125 +391,12 @@ __global__ void __launch_bounds__(1 << (L - 5)) k_feat_cta(const Launch P) {
 template <int L>
 __device__ __forceinline__ void chunked_item(const Launch& P, int64_t n, int e, float* sm, int tid,
                                              const float* __restrict__ Gov) {
-  using C = Chunked<L>;
-  using Y = Lay<10>;
   constexpr int d = 1 << L;
-  const int warp = tid >> 5, lane = tid & 31;
-  float* slot = sm + warp * C::SLOT;
-  const uint32_t sbase = smem_addr(sm);
-  const int64_t off = (int64_t)e * d + warp * 1024;
-  const uint32_t bmask = __ldg(P.a.maskA + (int64_t)e * (d / 32) + warp * 32 + lane);
-  uint32_t poff[16];
-  float gt[32];
-  {
-    const uint4* pb = reinterpret_cast<const uint4*>(P.a.permB + off) + lane;
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const uint4 v = __ldg(pb + m * 32);
-      poff[2 * m] = v.x | (v.y << 16);
-      poff[2 * m + 1] = v.z | (v.w << 16);
-    }
-    if (Gov) {  // an overriding G, read in natural order
-#pragma unroll
-      for (int j = 0; j < 32; ++j) gt[j] = __ldg(Gov + off + Y::kB(lane, j));
-    } else {
-      const float4* gb = reinterpret_cast<const float4*>(P.a.GB + off) + lane;
-#pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const float4 v = __ldg(gb + m * 32);
-        gt[4 * m] = v.x;
-        gt[4 * m + 1] = v.y;
-        gt[4 * m + 2] = v.z;
-        gt[4 * m + 3] = v.w;
-      }
-    }
-  }
-  // u = H B x-hat: index bits 0..9 per warp, then 10..L-1 across the chunks
-  {
-    float w[32];
-    const float* row = P.a.x + n * P.a.ldx;
-    const int64_t in_dim = P.a.in_dim;
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int k0 = warp * 1024 + Y::kA(lane, 4 * m);
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (P.vec_x) {
-        if (k0 < in_dim) v = __ldg(reinterpret_cast<const float4*>(row + k0));
-      } else {
-        if (k0 + 0 < in_dim) v.x = __ldg(row + k0 + 0);
-        if (k0 + 1 < in_dim) v.y = __ldg(row + k0 + 1);
-        if (k0 + 2 < in_dim) v.z = __ldg(row + k0 + 2);
-        if (k0 + 3 < in_dim) v.w = __ldg(row + k0 + 3);
-      }
-      w[4 * m] = v.x;
-      w[4 * m + 1] = v.y;
-      w[4 * m + 2] = v.z;
-      w[4 * m + 3] = v.w;
-    }
-    apply_signs(w, bmask);
-    hreg<Y::maskA()>(w);
-    store_A<10>(slot, 0, lane, w);
-    __syncwarp();
-    load_B<10>(slot, 0, lane, w);
-    hreg<Y::maskB()>(w);
-    __syncwarp();
-    store_B<10>(slot, 0, lane, w);
-  }
-  __syncthreads();
-  chunk_columns_inplace<L>(sm, tid);
-  __syncthreads();
-  // v = Pi u gathered into chunk `warp` (layout B), G, H over bits 0..9
-  float w[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j)
-    w[j] = lds32(sbase + 4u * ((j & 1) ? (poff[j >> 1] >> 16) : (poff[j >> 1] & 0xffffu)));
-  hreg_scaled<Y::maskB()>(w, gt);
-  __syncthreads();  // every warp has gathered: the slots may be rewritten
-  store_B<10>(slot, 0, lane, w);
-  __syncwarp();
-  load_A<10>(slot, 0, lane, w);
-  hreg<Y::maskA()>(w);
-  __syncwarp();
-  store_A<10>(slot, 0, lane, w);
-  __syncthreads();
-  // bits 10..L-1 of the second transform, then z = Cs h and [cos | sin]
-  const int64_t F = 2ll * P.a.E * d;
-  float* out = P.phi + n * F + 2ll * e * d;
-  const float* cs = P.a.Cs + (int64_t)e * d;
-#pragma unroll
-  for (int q = 0; q < C::CG; ++q) {
-    const int c0 = C::VEC * (tid + C::NT * q);
-    float u[C::W][C::VEC];
-#pragma unroll
-    for (int i = 0; i < C::W; ++i) ld_vec<C::VEC>(sm + i * C::SLOT + pad(c0), u[i]);
-#pragma unroll
-    for (int h = 1; h < C::W; h <<= 1)
-#pragma unroll
-      for (int i = 0; i < C::W; ++i)
-        if (!(i & h))
-#pragma unroll
-          for (int v = 0; v < C::VEC; ++v) {
-            const float a = u[i][v], b = u[i | h][v];
-            u[i][v] = a + b;
-            u[i | h][v] = a - b;
-          }
-#pragma unroll
-    for (int i = 0; i < C::W; ++i) {
-      const int k = c0 + 1024 * i;
-      float cv[C::VEC], co[C::VEC], si[C::VEC];
-      ld_vec<C::VEC>(cs + k, cv);
-#pragma unroll
-      for (int v = 0; v < C::VEC; ++v) cos_sin(cv[v] * u[i][v], co[v], si[v]);
-      if constexpr (C::VEC == 4) {
-        __stcs(reinterpret_cast<float4*>(out + k), make_float4(co[0], co[1], co[2], co[3]));
-        __stcs(reinterpret_cast<float4*>(out + d + k), make_float4(si[0], si[1], si[2], si[3]));
-      } else {
-        __stcs(reinterpret_cast<float2*>(out + k), make_float2(co[0], co[1]));
-        __stcs(reinterpret_cast<float2*>(out + d + k), make_float2(si[0], si[1]));
-      }
-    }
-  }
-  __syncthreads();  // the slots are read before the next item rewrites them
+  const int64_t eo = (int64_t)e * d;
+  chunked_map<L>(P.a.x + n * P.a.ldx, P.a.in_dim, P.vec_x, P.a.permB + eo,
+                 Gov ? nullptr : P.a.GB + eo, Gov ? Gov + eo : nullptr, P.a.maskA + eo / 32,
+                 P.a.Cs + eo, P.phi + n * 2ll * P.a.E * d + 2ll * e * d, sm, tid,
+                 [] { __syncthreads(); });
 }
 
 template <int L>  // 16 warps per SM at 128 registers (measured best; 64 registers spill)

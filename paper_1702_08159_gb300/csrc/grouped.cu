@@ -9,8 +9,9 @@
 //     feature kernel (register layouts A and B, lane-ordered tables);
 //     16 * grain steps form a unit.
 //   * d >= 2048: "block items" -- one (vector, expansion) for a sub-block of
-//     2^(L-5) threads; 512/2^(L-5) items of the same d form a unit, each
-//     sub-block synchronising on its own named barrier.
+//     2^(L-5) threads in the chunked block form (one 1024-float chunk per
+//     warp); 512/2^(L-5) items of the same d form a unit, each sub-block
+//     synchronising on its own named barrier.
 // Units are ordered by estimated cost, largest first. The persistent kernel
 // runs one 512-thread block per SM; a block takes the next unit with one
 // atomicAdd on a counter (no thread ever waits for another block) until the
@@ -188,54 +189,18 @@ __device__ void warp_step(const GArgs& a, const GStep& st, float* buf, int lane)
   __syncwarp();
 }
 
-// One block item (11 <= L <= 14) on a sub-block of T threads with barrier `bar`.
+// One block item (11 <= L <= 14): the chunked block form of the map on a
+// sub-block of 2^(L-5) threads (2^(L-10) warps, one 1024-float chunk each)
+// that synchronises on its own named barrier `bar`.
 template <int L>
-__device__ void block_item(const GArgs& a, const GItem& it, float* buf, int lam, int bar) {
-  using Y = Lay<L>;
-  constexpr int d = Y::d, T = Y::T;
+__device__ void block_item(const GArgs& a, const GItem& it, float* buf, int tid, int bar) {
+  constexpr int d = 1 << L;
   const GPlan pl = a.plans[it.plan];
   const GVec v = a.vecs[it.vec];
-  const int64_t off = (int64_t)it.e * d;
-  const uint32_t buf_addr = smem_addr(buf);
-  float w[32];
-  load_row_A<L>(a.x + v.x_off, v.in_dim, a.vec_x, true, lam, w);
-  uint32_t mask = 0;
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const int k0 = Y::kA(lam, 4 * m);
-    mask |= ((__ldg(pl.bits + (int64_t)it.e * (d / 32) + (k0 >> 5)) >> (k0 & 31)) & 0xFu) << (4 * m);
-  }
-  apply_signs(w, mask);
-  hreg<Y::maskA()>(w);
-  store_A<L>(buf, 0, lam, w);
-  named_barrier(bar, T);
-  load_B<L>(buf, 0, lam, w);
-  hreg<Y::maskB()>(w);
-  store_B<L>(buf, 0, lam, w);
-  named_barrier(bar, T);
-  load_C<L>(buf, lam, w);
-  hreg<Y::maskC()>(w);
-  store_C<L>(buf, lam, w);
-  named_barrier(bar, T);
-  float gt[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    const int k = Y::kC(lam, j);
-    gt[j] = __ldg(pl.G + off + k);
-    w[j] = lds32(buf_addr + 4u * (uint32_t)spos<L>(0, (int)__ldg(pl.perm + off + k)));
-  }
-  hreg_scaled<Y::maskC()>(w, gt);
-  named_barrier(bar, T);
-  store_C<L>(buf, lam, w);
-  named_barrier(bar, T);
-  load_B<L>(buf, 0, lam, w);
-  hreg<Y::maskB()>(w);
-  store_B<L>(buf, 0, lam, w);
-  named_barrier(bar, T);
-  load_A<L>(buf, 0, lam, w);
-  hreg<Y::maskA()>(w);
-  store_features_A<L>(a.phi + v.phi_off + 2 * off, lam, w, pl.Cs + off);
-  named_barrier(bar, T);
+  const int64_t eo = (int64_t)it.e * d;
+  chunked_map<L>(a.x + v.x_off, v.in_dim, a.vec_x, pl.permB + eo, pl.GB + eo, nullptr,
+                 pl.maskA + eo / 32, pl.Cs + eo, a.phi + v.phi_off + 2 * eo, buf, tid,
+                 [bar] { named_barrier(bar, Chunked<L>::NT); });
 }
 
 __global__ void __launch_bounds__(kGThreads, 1) k_grouped(const GArgs a) {
