@@ -166,14 +166,6 @@ __device__ __forceinline__ void named_barrier(int id, int threads) {
 __device__ __forceinline__ void named_arrive(int id, int threads) {
   asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
-// Streaming (evict-first) 128-bit global store: the feature matrix is written
-// once and not re-read by the kernel, so it should not displace the tables.
-__device__ __forceinline__ void stg128_cs(float* p, float a, float b, float c, float d) {
-  asm volatile("st.global.cs.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
-               "f"(d)
-               : "memory");
-}
-
 // ---------------------------------------------------------------------------
 // Layout moves through shared memory. `buf` points at the caller's shared
 // buffer; g is the vector slot of this thread's group. Callers separate a

@@ -10,15 +10,19 @@
 //   dCs += h dz            dh = Cs dz         dw = H dh
 //   dG  += v dw            dv = G dw          du[pi(k)] = dv[k]      du0 = H du
 //   dx  += (B du0)[:in_dim]
-// Two warp kernels share that per-sample core:
-//   k_bwd_params  work items (tile of samples, expansion), expansion-major,
-//                 accumulate dCs, dG per warp, write one partial row per warp;
-//                 k_reduce_params sums the rows of each expansion in order.
+// Two kernels share that per-sample core:
+//   k_bwd_params  a block of 8 warps per (expansion, range of samples): G_e,
+//                 Cs_e (and, fused, W_e or the block's dphi rows) staged in
+//                 shared memory; per-warp running sums of h dz and v dw,
+//                 added over the warps in order into one partial row per
+//                 block; k_reduce_params sums the rows of each expansion in
+//                 order.
 //   k_bwd_input   each warp owns samples and loops over all expansions,
 //                 accumulating dx in registers (no cross-warp sum needed).
-// With fused logits the upstream gradient is dphi = W^T dlogits, formed on
-// the fly from W; k_bwd_params then also writes the recomputed features so
-// k_logit_weight_grads can form dW = dlogits^T phi and db = sum dlogits.
+// With fused logits the upstream gradient is dphi = W^T dlogits, formed
+// from W (at d = 1024 for 8 rows at a time by the whole block);
+// k_bwd_params then also writes the recomputed features so k_weight_grads
+// can form dW = dlogits^T phi and db = sum dlogits in one launch.
 // All sums run in a fixed order, so results are bit-reproducible.
 #include <cuda_runtime.h>
 
@@ -81,9 +85,7 @@ __global__ void __launch_bounds__(1024) k_softmax_xent(const float* __restrict__
 template <int L>
 struct BShape {
   static constexpr int T = Lay<L>::T;
-  static constexpr int VPW = 32 / T;
-  static constexpr int R = VPW >= 8 ? 1 : 8 / VPW;
-  static constexpr int SPI = VPW * R;
+  static constexpr int VPW = 32 / T;  // samples a warp holds at once
 };
 
 struct BwdLaunch {
