@@ -51,7 +51,9 @@ typedef void* mck_stream_t;            /* a cudaStream_t */
 
 typedef enum {
   MCK_RBF = 0,    /* Gaussian RBF kernel exp(-|x-x'|^2/(2 sigma^2)) (Eq. etn:rbf) */
-  MCK_MATERN = 1  /* RBF Matern: C_kk = |sum of t uniform unit-ball points| (Sec. "Customizing McKernel") */
+  MCK_MATERN = 1, /* RBF Matern: C_kk = |sum of t uniform unit-ball points| (Sec. "Customizing McKernel") */
+  MCK_LAPLACE = 2 /* Laplacian exp(-|x-x'|/sigma): C_kk ~ chi_d/|N(0,1)|, the spherical Cauchy radius,
+                     one more radial spectral distribution (Sec. "McKernel", item C) */
 } mck_kernel_t;
 
 typedef enum {
@@ -80,7 +82,7 @@ typedef enum {
  * Description": factory pattern, parameters from a hash).
  *   d       padded dimension, a power of two, 2 <= d <= 2^15
  *   E       number of expansions, 1 <= E <= 65536
- *   kernel  MCK_RBF or MCK_MATERN
+ *   kernel  MCK_RBF, MCK_MATERN or MCK_LAPLACE
  *   sigma   kernel width, finite and > 0 (the sigma of Eq. etn:mckernel)
  *   seed    64-bit hash key; equal seeds give bit-identical B and Pi
  * The Matern order t defaults to 40 (the paper's experiments, Fig. 2-4

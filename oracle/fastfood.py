@@ -21,7 +21,8 @@ Random draws come from Philox4x32-10 (``oracle.philox``) with the counter
 layout (c0, c1, c2, c3) = (index, expansion e, tag, sub-draw) and key = the
 64-bit seed split into two words. Tags:
   1 B sign, 2 Fisher-Yates draw, 3 G, 4 RBF radius (Marsaglia-Tsang trial),
-  5 Matern ball coordinates (c2 = 5 + 16*k), 6 Matern ball radius.
+  5 Matern ball coordinates (c2 = 5 + 16*k), 6 Matern ball radius,
+  7 the normal divisor of the Laplacian radius.
 
 Readings of points the paper leaves open (each also listed in the design doc):
   * B[k] = -1 when bit 0 of word 0 is set, else +1.
@@ -37,6 +38,11 @@ Readings of points the paper leaves open (each also listed in the design doc):
   * Matern calibration, the paper's algorithm literally: r_k = || sum_{j=1..t}
     u_j || with u_j = U_j^{1/d} X_j/||X_j||, X_j ~ N(0, I_d), U_j ~ U(0,1];
     again C[k] = r_k / ||G_e||_2.
+  * Laplacian calibration, one more "radial spectral distribution" (Sec.
+    "McKernel", item C): the kernel exp(-||x - y|| / sigma) has the spherical
+    multivariate Cauchy as spectral density, whose radius is chi_d / |N(0,1)|;
+    r_k = (the RBF radius) / max(|n_k|, 2**-32) with n_k the Box-Muller
+    (cosine) normal of counter (k, e, 7, 0); again C[k] = r_k / ||G_e||_2.
   * The 1/(sigma sqrt d) factor is applied with C: Cs = C / (sigma sqrt d).
   * phi = [cos | sin] per expansion block, no 1/sqrt(E d) normalisation.
   * x-hat = x followed by zeros (padding at the end).
@@ -58,9 +64,11 @@ TAG_G = 3
 TAG_RBF = 4
 TAG_BALL = 5
 TAG_BALL_RADIUS = 6
+TAG_LAPLACE = 7
 
 RBF = 0
 MATERN = 1
+LAPLACE = 2
 
 TWO_M32 = 2.0 ** -32
 
@@ -212,6 +220,16 @@ def ball_sum_norm(d, e, k, t, seed):
     return float(np.linalg.norm(u.sum(axis=0)))
 
 
+def laplace_radius(d, e, k, seed):
+    """r = chi_d / |N(0,1)|: the radius of the spherical multivariate Cauchy,
+    the spectral density of exp(-||x - y||) (a multivariate t with one degree
+    of freedom: z / |n| with z ~ N(0, I_d), n ~ N(0, 1) independent). The
+    divisor is floored at 2**-32 (a zero draw has probability 2**-32)."""
+    w0, w1, _, _ = _words(np.uint64(k), np.uint64(e), TAG_LAPLACE, 0, seed)
+    n, _ = box_muller(w0, w1)
+    return rbf_radius(d, e, k, seed) / max(abs(float(n)), TWO_M32)
+
+
 def table_radius(d, E, kernel, t, seed, ks=None):
     """Row norms r_e[k] of the calibration, shape (E, len(ks))."""
     ks = range(d) if ks is None else ks
@@ -220,6 +238,8 @@ def table_radius(d, E, kernel, t, seed, ks=None):
         for i, k in enumerate(ks):
             if kernel == RBF:
                 out[e, i] = rbf_radius(d, e, k, seed)
+            elif kernel == LAPLACE:
+                out[e, i] = laplace_radius(d, e, k, seed)
             else:
                 out[e, i] = ball_sum_norm(d, e, k, t, seed)
     return out

@@ -28,7 +28,7 @@ __all__ = [
     "fused_logits_backward", "softmax_xent", "library_path",
 ]
 
-_KERNELS = {"rbf": _lib.MCK_RBF, "matern": _lib.MCK_MATERN}
+_KERNELS = {"rbf": _lib.MCK_RBF, "matern": _lib.MCK_MATERN, "laplace": _lib.MCK_LAPLACE}
 
 
 def library_path():
@@ -126,7 +126,8 @@ class Plan:
             pass
 
     def __repr__(self):
-        k = "rbf" if self.kernel == _lib.MCK_RBF else f"matern(t={self.matern_t})"
+        k = {_lib.MCK_RBF: "rbf", _lib.MCK_LAPLACE: "laplace"}.get(
+            self.kernel, f"matern(t={self.matern_t})")
         return f"Plan(d={self.d}, E={self.E}, kernel={k}, sigma={self.sigma}, seed={self.seed})"
 
 

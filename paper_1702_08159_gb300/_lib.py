@@ -18,6 +18,7 @@ MCK_EUNSUPPORTED = -5
 
 MCK_RBF = 0
 MCK_MATERN = 1
+MCK_LAPLACE = 2
 MCK_FP32 = 0
 MCK_BF16 = 1
 MCK_FP16 = 2

@@ -228,7 +228,7 @@ mck_status_t mck_plan_ex(mck_plan_t* out, int64_t d, int32_t E, int32_t kernel, 
     return fail(MCK_EUNSUPPORTED, "plans support d <= 2^15");
   if (E < 1 || E > 65536) return fail(MCK_EINVAL, "E must be in [1, 65536]");
   if ((int64_t)E * d > ((int64_t)1 << 28)) return fail(MCK_EINVAL, "E * d must be <= 2^28");
-  if (kernel != MCK_RBF && kernel != MCK_MATERN) return fail(MCK_EINVAL, "unknown kernel");
+  if (kernel != MCK_RBF && kernel != MCK_MATERN && kernel != MCK_LAPLACE) return fail(MCK_EINVAL, "unknown kernel");
   if (!(sigma > 0.0) || !std::isfinite(sigma)) return fail(MCK_EINVAL, "sigma must be finite and > 0");
   if (kernel == MCK_MATERN && (matern_t < 1 || matern_t > 4096))
     return fail(MCK_EINVAL, "Matern t must be in [1, 4096]");

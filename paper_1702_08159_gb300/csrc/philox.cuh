@@ -50,6 +50,7 @@ enum : uint32_t {
   kTagRbf = 4,         // Marsaglia-Tsang trial j of radius k at (k, e, 4, j)
   kTagBall = 5,        // Matern ball point j, coords 2p, 2p+1 at (p, e, 5 + 16 k, j)
   kTagBallRadius = 6,  // Matern ball point j radius draw at (k, e, 6, j)
+  kTagLaplace = 7,     // normal divisor of Laplacian radius k at (k, e, 7, 0)
 };
 
 }  // namespace mck

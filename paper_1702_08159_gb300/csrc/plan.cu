@@ -79,6 +79,11 @@ __global__ void k_plan_norm(const double* __restrict__ G64, double* __restrict__
 // dd = d/2 - 1/3, c = 1/sqrt(9 dd); trial j draws g ~ N(0,1) (words 0, 1) and
 // U (word 2) from counter (k, e, 4, j); v = (1 + c g)^3 > 0 is accepted when
 // ln U < g^2/2 + dd - dd v + dd ln v; then r^2 = 2 dd v. Cs = r/||G_e||/(sigma sqrt d).
+// LAPLACE: the Laplacian kernel exp(-|x - x'|/sigma) has the spherical
+// multivariate Cauchy as spectral density, a radius chi_d / |N(0,1)|: r is
+// divided by |n|, n the Box-Muller normal (words 0, 1) of counter (k, e, 7, 0),
+// floored at 2^-32.
+template <bool LAPLACE>
 __global__ void k_plan_rbf(float* __restrict__ Cs, const double* __restrict__ norm, int64_t d,
                            int32_t E, double inv_sigma_sqrt_d, uint32_t k0, uint32_t k1) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -99,6 +104,10 @@ __global__ void k_plan_rbf(float* __restrict__ Cs, const double* __restrict__ no
       r = sqrt(2.0 * dd * v);
       break;
     }
+  }
+  if (LAPLACE) {
+    const U32x4 w = philox4x32_10(k, e, kTagLaplace, 0, k0, k1);
+    r /= fmax(fabs(box_muller_cos(w.x, w.y)), 0x1p-32);
   }
   Cs[t] = (float)((r / norm[e]) * inv_sigma_sqrt_d);
 }
@@ -327,7 +336,9 @@ mck_status_t build_tables(mck_plan_s* p, cudaStream_t s) {
   k_plan_norm<<<(unsigned)E, 1024, 0, s>>>(G64, norm, d);
   const double inv = 1.0 / (p->sigma * std::sqrt((double)d));
   if (p->kernel == MCK_RBF) {
-    k_plan_rbf<<<blocks_for(n, 128), 128, 0, s>>>(p->Cs, norm, d, p->E, inv, k0, k1);
+    k_plan_rbf<false><<<blocks_for(n, 128), 128, 0, s>>>(p->Cs, norm, d, p->E, inv, k0, k1);
+  } else if (p->kernel == MCK_LAPLACE) {
+    k_plan_rbf<true><<<blocks_for(n, 128), 128, 0, s>>>(p->Cs, norm, d, p->E, inv, k0, k1);
   } else {
     const int64_t pairs = d / 2;
     int threads = (int)((pairs + kBallPairs - 1) / kBallPairs);

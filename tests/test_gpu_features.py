@@ -115,6 +115,33 @@ def test_matern(mck, dev, d):
     assert _max_err(phi, ref) <= TOL
 
 
+@pytest.mark.parametrize("d,E,n", [(8, 3, 5), (64, 3, 7), (1024, 3, 9), (4096, 2, 3)])
+def test_laplace(mck, dev, d, E, n):
+    """Laplacian calibration through the same kernels. Its radii are heavy
+    tailed (chi_d over |N(0,1)|), so a few phases are far larger than the
+    RBF's: the bar adds, per phase, float32's resolution of z and the
+    rounding of the transform, 2^-24 (|z_k| + 4 log2(d) Cs_k max_j |h_j|),
+    with the oracle run on the plan's own float32 Cs (whose parity with the
+    float64 tables is checked with the tables). Phases past 2e5, where float32
+    no longer resolves a period to 1e-5 at all, are only checked to be
+    bounded."""
+    plan = mck.Plan(d, E, "laplace", 3.0, 2024 + d)
+    x = wl.mnist_like(n, min(d, 784), seed=d)
+    phi = mck.features(plan, torch.from_numpy(x).to(dev)).cpu().numpy().astype(np.float64)
+    T = dict(_oracle_tables(plan), Cs=plan.tables()["Cs"].astype(np.float64))
+    z = ff.phases(x.astype(np.float64), T)                      # (n, E, d)
+    Cs = T["Cs"][None]
+    hmax = np.abs(z / Cs).max(axis=2, keepdims=True)
+    tol = TOL + 2.0 ** -24 * (np.abs(z) + 4 * max(np.log2(d), 1) * Cs * hmax)
+    big = np.abs(z) > 2e5
+    tol = np.where(big, 2.0, tol)
+    tol = np.concatenate([tol, tol], axis=2).reshape(n, -1)
+    ref = ff.features(x.astype(np.float64), T)
+    assert np.all(np.abs(phi - ref) <= tol), float((np.abs(phi - ref) - tol).max())
+    assert np.all(np.abs(phi) <= 1.0 + 1e-6)
+    plan.close()
+
+
 def test_deterministic(mck, dev):
     plan = mck.Plan(1024, 4, "rbf", 1.0, 42)
     x = torch.from_numpy(wl.mnist_like(100, 784, seed=1)).to(dev)

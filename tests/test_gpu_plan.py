@@ -32,6 +32,22 @@ def test_rbf_tables(mck, d, E, seed):
     plan.close()
 
 
+@pytest.mark.parametrize("d,E,seed", [(2, 3, 0), (16, 3, 42), (1024, 4, 42), (4096, 2, 11)])
+def test_laplace_tables(mck, d, E, seed):
+    """Laplacian calibration: the chi_d radius over |N(0,1)|, float64 on both
+    sides and rounded to float32 once."""
+    sigma = 0.8
+    plan = mck.Plan(d, E, "laplace", sigma, seed)
+    t = plan.tables()
+    ref = ff.plan_tables(d, E, ff.LAPLACE, sigma, seed=seed)
+    np.testing.assert_array_equal(t["perm"].astype(np.int64), ref["perm"])
+    c32 = ref["Cs"].astype(np.float32)
+    assert np.all(t["Cs"] > 0)
+    assert np.all(np.abs(t["Cs"].astype(np.float64) - ref["Cs"]) <= np.spacing(np.abs(c32)))
+    assert "laplace" in repr(plan)
+    plan.close()
+
+
 @pytest.mark.parametrize("d,E,t", [(2, 2, 3), (64, 2, 40), (256, 1, 40), (1024, 1, 40)])
 def test_matern_tables(mck, d, E, t):
     sigma = 1.0

@@ -59,6 +59,20 @@ def test_rbf_kernel_approximation(s):
     assert abs(phi[0] @ phi[0] / (E * d) - 1.0) < 1e-12
 
 
+@pytest.mark.parametrize("s", [0.25, 0.5, 1.0])
+def test_laplace_kernel_approximation(s):
+    # |w_k| = r_k / sigma with r_k ~ chi_d/|N(0,1)| and a (nearly) uniform
+    # direction: E cos(w . Delta) = exp(-||Delta|| / sigma), the Laplacian kernel.
+    d, E, sigma = 64, 64, 1.5
+    T = ff.plan_tables(d, E, ff.LAPLACE, sigma, seed=33)
+    x, y = _pair(d, s * sigma, seed=int(s * 100) + 1)
+    phi = ff.features(np.stack([x, y]), T)
+    est = phi[0] @ phi[1] / (E * d)
+    assert abs(est - math.exp(-s)) < 5 / math.sqrt(E * d)
+    # at these distances the Gaussian's value lies outside the bar
+    assert abs(math.exp(-s) - math.exp(-s * s / 2)) > 5 / math.sqrt(E * d)
+
+
 def _ball_charfn(d, s):
     """E exp(i w.u) for u uniform in the unit d-ball, |w| = s: Gamma(d/2+1) (2/s)^{d/2} J_{d/2}(s)."""
     nu = d / 2.0

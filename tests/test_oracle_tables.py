@@ -82,6 +82,19 @@ def test_rbf_radius_is_chi_d(d):
     assert scipy.stats.kstest(r, scipy.stats.chi(d).cdf).pvalue > 1e-4
 
 
+@pytest.mark.parametrize("d", [4, 64])
+def test_laplace_radius_is_spherical_cauchy(d):
+    # The spherical multivariate Cauchy (the Laplacian kernel's spectral
+    # density) is z/|n| with z ~ N(0, I_d), n ~ N(0, 1) independent, so
+    # r^2/d = (chi2_d/d)/(chi2_1/1) ~ F(d, 1); r > 0 always.
+    r = ff.table_radius(d, 1, ff.LAPLACE, 0, seed=19, ks=range(3000))[0]
+    assert np.all(r > 0)
+    assert scipy.stats.kstest(r ** 2 / d, scipy.stats.f(d, 1).cdf).pvalue > 1e-4
+    # the divisor is drawn independently of the chi_d radius of the same k
+    q = r / ff.table_radius(d, 1, ff.RBF, 0, seed=19, ks=range(3000))[0]
+    assert scipy.stats.kstest(1.0 / q, scipy.stats.halfnorm.cdf).pvalue > 1e-4
+
+
 def test_matern_single_sample_is_ball_radius():
     # t = 1: ||u_1|| = U^{1/d}, so ||u_1||^d ~ U(0,1) (Sec. "Customizing McKernel": P(R <= r) = r^n).
     d = 8
