@@ -114,6 +114,17 @@ mck_status_t mck_plan_info(mck_plan_t plan, int64_t* d, int32_t* E, int32_t* ker
 mck_status_t mck_plan_tables(mck_plan_t plan, uint32_t* B_bits, uint32_t* perm, float* G,
                              float* Cs);
 
+/* Replace the plan's sign diagonals B (Sec. "Empirical Analysis": learning
+ * B, which the paper likens to attention; a trainer keeps real values and
+ * uses their signs).
+ *   B  device E x d float32: B_e[k] becomes -1 where B[e][k] < 0 and +1
+ *      otherwise (0 and NaN give +1).
+ * Stream-ordered on `stream`: work queued after it on that stream sees the
+ * new signs; the caller orders other streams, and must not change the signs
+ * while a group or a captured graph that uses the plan runs. Returns
+ * MCK_EINVAL for a NULL plan or B. Pi, G and C are unchanged. */
+mck_status_t mck_plan_set_signs(mck_plan_t plan, const float* B, mck_stream_t stream);
+
 /* In-place unnormalised Walsh-Hadamard transform of n vectors of length d
  * (Sec. "Fast Walsh Hadamard": H_n = [[H_{n-1}, H_{n-1}], [H_{n-1}, -H_{n-1}]]).
  *   x     device, n x d float32, contiguous, 16-byte aligned when d >= 4
@@ -150,6 +161,16 @@ mck_status_t mck_features_backward(mck_plan_t plan, const float* x, int64_t n, i
                                    int64_t ldx, const float* Cs, const float* G,
                                    const float* dphi, float* dx, float* dCs, float* dG,
                                    mck_stream_t stream);
+
+/* mck_features_backward plus the gradient with respect to B read as a real
+ * diagonal (u0 = B x-hat, linear in B):
+ *   dB    device E x d or NULL: sum over samples of x-hat * du0, with du0 the
+ *         gradient reaching u0 (zero at k >= in_dim, where x-hat is padding)
+ * With dB the scratch memory is 3 E d x 4 bytes per 8 samples. */
+mck_status_t mck_features_backward_ex(mck_plan_t plan, const float* x, int64_t n,
+                                      int64_t in_dim, int64_t ldx, const float* Cs,
+                                      const float* G, const float* dphi, float* dx, float* dCs,
+                                      float* dG, float* dB, mck_stream_t stream);
 
 /* logits = phi(x) W^T + b without writing phi to memory (Sec. "Empirical
  * Analysis": softmax(W phi + b); the softmax itself is mck_softmax_xent).
@@ -200,6 +221,15 @@ mck_status_t mck_fused_logits_backward(mck_plan_t plan, const float* x, int64_t 
                                        const float* G, const float* W, int32_t num_classes,
                                        const float* dlogits, float* dx, float* dCs, float* dG,
                                        float* dW, float* db, mck_stream_t stream);
+
+/* mck_fused_logits_backward plus dB (device E x d or NULL), the gradient with
+ * respect to B read as a real diagonal, as in mck_features_backward_ex. */
+mck_status_t mck_fused_logits_backward_ex(mck_plan_t plan, const float* x, int64_t n,
+                                          int64_t in_dim, int64_t ldx, const float* Cs,
+                                          const float* G, const float* W, int32_t num_classes,
+                                          const float* dlogits, float* dx, float* dCs,
+                                          float* dG, float* dB, float* dW, float* db,
+                                          mck_stream_t stream);
 
 /* ---- Uneven batches in one persistent launch -------------------------------
  * A group is a prepared batch of vectors of different padded dimensions,

@@ -8,8 +8,11 @@ softmax(W phi(Z-hat x-hat) + b). The paper's loss (Eq. etn:loss) is the
 logistic loss log(1 + exp(-y f)); with C classes its multi-class form is the
 softmax cross-entropy -log softmax(l)_y, which equals the logistic loss when
 C = 2 (tests check that reduction). Sec. "Empirical Analysis" also proposes
-learning the calibration C and G by backpropagation, so gradients are given
-with respect to x, Cs (= C/(sigma sqrt d)), G, W and b.
+learning the calibration C and G by backpropagation, and learning B (which
+it likens to attention), so gradients are given with respect to x, Cs
+(= C/(sigma sqrt d)), G, W, b and B. For B the map is read with B as a real
+diagonal (u0 = B x-hat, linear in B); a trainer that keeps B in {+1, -1}
+passes this gradient through the sign (straight-through).
 
 Gradients follow the chain rule through each stage of
 z = Cs H G Pi H B x-hat using H^T = H and Pi^T = Pi^{-1}:
@@ -17,6 +20,7 @@ z = Cs H G Pi H B x-hat using H^T = H and Pi^T = Pi^{-1}:
   dCs = sum_n h * dz,   dh = Cs * dz,   dw = H dh
   dG  = sum_n v * dw,   dv = G * dw,    du[perm[k]] = dv[k],   du0 = H du
   dx  = sum_e (B * du0)[:in_dim]
+  dB  = sum_n x-hat * du0
 Pinned by central finite differences of ``loss`` (tests/test_oracle_training.py).
 """
 
@@ -48,8 +52,9 @@ def loss(x, T, W, b, y):
     return softmax_xent(logits(phi, W, b), y)[0]
 
 
-def features_backward(x, T, dphi):
-    """Gradients of sum(phi * dphi) w.r.t. x, Cs and G (chain rule, see header)."""
+def features_backward(x, T, dphi, with_dB=False):
+    """Gradients of sum(phi * dphi) w.r.t. x, Cs and G (chain rule, see header);
+    with ``with_dB`` also w.r.t. the diagonal B, as a fourth result."""
     B, perm, G, Cs = T["B"], T["perm"], T["G"], T["Cs"]
     E, d = B.shape
     N, in_dim = x.shape
@@ -57,6 +62,8 @@ def features_backward(x, T, dphi):
     dx_hat = np.zeros((N, d))
     dCs = np.zeros((E, d))
     dG = np.zeros((E, d))
+    dB = np.zeros((E, d))
+    xh = ff.pad(x, d)
     for e in range(E):
         s = ff.stages(x, B[e], perm[e], G[e], Cs[e])
         z = s["z"]
@@ -70,6 +77,9 @@ def features_backward(x, T, dphi):
         du[:, perm[e]] = dv
         du0 = ff.fwht(du)
         dx_hat += B[e] * du0
+        dB[e] = (xh * du0).sum(axis=0)
+    if with_dB:
+        return dx_hat[:, :in_dim], dCs, dG, dB
     return dx_hat[:, :in_dim], dCs, dG
 
 
@@ -81,9 +91,9 @@ def train_grads(x, T, W, b, y):
     dW = dl.T @ phi
     db = dl.sum(axis=0)
     dphi = dl @ W
-    dx, dCs, dG = features_backward(x, T, dphi)
+    dx, dCs, dG, dB = features_backward(x, T, dphi, with_dB=True)
     return {"loss": L, "logits": l, "dlogits": dl, "dW": dW, "db": db,
-            "dx": dx, "dCs": dCs, "dG": dG}
+            "dx": dx, "dCs": dCs, "dG": dG, "dB": dB}
 
 
 def finite_difference(f, a, idx, h=1e-6):

@@ -112,7 +112,18 @@ class Plan:
         """B as an (E, d) float32 array of +-1."""
         bits = self.tables()["B_bits"]
         k = np.arange(self.d)
-        return np.where((bits[:, k // 32] >> (k % 32)) & 1, -1.0, 1.0).astype(np.float32)
+        return np.ascontiguousarray(
+            np.where((bits[:, k // 32] >> (k % 32)) & 1, -1.0, 1.0), dtype=np.float32)
+
+    def set_signs(self, B):
+        """Replace the sign diagonals: B_e[k] = -1 where B[e, k] < 0, else +1.
+        B is a contiguous (E, d) float32 tensor on the plan's device; the
+        update is ordered on the current stream."""
+        _f32_cuda(B, "B", self.device)
+        if tuple(B.shape) != (self.E, self.d) or not B.is_contiguous():
+            raise ValueError(f"B must be a contiguous ({self.E}, {self.d}) tensor")
+        check(load().mck_plan_set_signs(self.handle, _ptr(B), _stream(B.device)),
+              "mck_plan_set_signs")
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -175,8 +186,11 @@ def features(plan, x, Cs=None, G=None, out=None):
     return out
 
 
-def features_backward(plan, x, dphi, Cs=None, G=None, need_dx=True, need_dCs=True, need_dG=True):
-    """(dx, dCs, dG) of sum(phi(x) * dphi); entries not requested are None."""
+def features_backward(plan, x, dphi, Cs=None, G=None, need_dx=True, need_dCs=True, need_dG=True,
+                      need_dB=False):
+    """(dx, dCs, dG) of sum(phi(x) * dphi), and dB (B read as a real
+    diagonal) as a fourth entry when ``need_dB``; entries not requested are
+    None."""
     _f32_cuda(x, "x", plan.device)
     x, n, in_dim, ld = _rows(x)
     Cs, G = _tables(plan, Cs, G)
@@ -185,14 +199,15 @@ def features_backward(plan, x, dphi, Cs=None, G=None, need_dx=True, need_dCs=Tru
     dx = torch.empty((n, in_dim), device=dev, dtype=torch.float32) if need_dx else None
     dCs = torch.empty((plan.E, plan.d), device=dev, dtype=torch.float32) if need_dCs else None
     dG = torch.empty((plan.E, plan.d), device=dev, dtype=torch.float32) if need_dG else None
-    ldx = in_dim
+    dB = torch.empty((plan.E, plan.d), device=dev, dtype=torch.float32) if need_dB else None
     if dx is not None and ld != in_dim:
         x = x.contiguous()
         ld = in_dim
-    check(load().mck_features_backward(plan.handle, _ptr(x), n, in_dim, ld, _ptr(Cs), _ptr(G),
-                                       _ptr(dphi), _ptr(dx), _ptr(dCs), _ptr(dG), _stream(dev)),
+    check(load().mck_features_backward_ex(plan.handle, _ptr(x), n, in_dim, ld, _ptr(Cs), _ptr(G),
+                                          _ptr(dphi), _ptr(dx), _ptr(dCs), _ptr(dG), _ptr(dB),
+                                          _stream(dev)),
           "mck_features_backward")
-    return dx, dCs, dG
+    return (dx, dCs, dG, dB) if need_dB else (dx, dCs, dG)
 
 
 def fused_logits(plan, x, W, b=None, Cs=None, G=None, out=None):
@@ -214,8 +229,9 @@ def fused_logits(plan, x, W, b=None, Cs=None, G=None, out=None):
 
 
 def fused_logits_backward(plan, x, W, dlogits, Cs=None, G=None, need_dx=False, need_dCs=True,
-                          need_dG=True, need_dW=True, need_db=True):
-    """Gradients of sum(logits * dlogits) for fused_logits; dict of dx, dCs, dG, dW, db."""
+                          need_dG=True, need_dW=True, need_db=True, need_dB=False):
+    """Gradients of sum(logits * dlogits) for fused_logits; dict of dx, dCs,
+    dG, dB (B read as a real diagonal), dW and db (None where not requested)."""
     _f32_cuda(x, "x", plan.device)
     x, n, in_dim, ld = _rows(x)
     Cs, G = _tables(plan, Cs, G)
@@ -228,11 +244,12 @@ def fused_logits_backward(plan, x, W, dlogits, Cs=None, G=None, need_dx=False, n
         ld = in_dim
     mk = lambda need, shape: torch.empty(shape, device=dev, dtype=torch.float32) if need else None
     g = {"dx": mk(need_dx, (n, in_dim)), "dCs": mk(need_dCs, (plan.E, plan.d)),
-         "dG": mk(need_dG, (plan.E, plan.d)), "dW": mk(need_dW, tuple(W.shape)),
-         "db": mk(need_db, (C,))}
-    check(load().mck_fused_logits_backward(
+         "dG": mk(need_dG, (plan.E, plan.d)), "dB": mk(need_dB, (plan.E, plan.d)),
+         "dW": mk(need_dW, tuple(W.shape)), "db": mk(need_db, (C,))}
+    check(load().mck_fused_logits_backward_ex(
         plan.handle, _ptr(x), n, in_dim, ld, _ptr(Cs), _ptr(G), _ptr(W), C, _ptr(dlogits),
-        _ptr(g["dx"]), _ptr(g["dCs"]), _ptr(g["dG"]), _ptr(g["dW"]), _ptr(g["db"]), _stream(dev)),
+        _ptr(g["dx"]), _ptr(g["dCs"]), _ptr(g["dG"]), _ptr(g["dB"]), _ptr(g["dW"]), _ptr(g["db"]),
+        _stream(dev)),
         "mck_fused_logits_backward")
     return g
 
@@ -307,6 +324,16 @@ class Group:
                                     ctypes.byref(g)), "mck_group_info")
         return {"units": u.value, "warp_steps": s.value, "block_items": b.value,
                 "grain": g.value}
+
+    def set_signs(self, B):
+        """Replace the sign diagonals: B_e[k] = -1 where B[e, k] < 0, else +1.
+        B is a contiguous (E, d) float32 tensor on the plan's device; the
+        update is ordered on the current stream."""
+        _f32_cuda(B, "B", self.device)
+        if tuple(B.shape) != (self.E, self.d) or not B.is_contiguous():
+            raise ValueError(f"B must be a contiguous ({self.E}, {self.d}) tensor")
+        check(load().mck_plan_set_signs(self.handle, _ptr(B), _stream(B.device)),
+              "mck_plan_set_signs")
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

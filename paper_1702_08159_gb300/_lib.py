@@ -46,13 +46,18 @@ SIGNATURES = {
                             ctypes.POINTER(_D), ctypes.POINTER(_I32), ctypes.POINTER(_U64),
                             ctypes.POINTER(_I32)]),
     "mck_plan_tables": (_ST, [_P, _P, _P, _P, _P]),
+    "mck_plan_set_signs": (_ST, [_P, _P, _P]),
     "mck_fwht": (_ST, [_P, _I64, _I64, _I32, _P]),
     "mck_features": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P]),
     "mck_features_backward": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, _P]),
+    "mck_features_backward_ex": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, _P,
+                                       _P]),
     "mck_fused_logits": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _I32, _P, _P]),
     "mck_fused_logits_noalloc": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _I32, _P, _P]),
     "mck_fused_logits_backward": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _I32, _P, _P, _P,
                                         _P, _P, _P, _P]),
+    "mck_fused_logits_backward_ex": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _I32, _P, _P,
+                                           _P, _P, _P, _P, _P, _P]),
     "mck_softmax_xent": (_ST, [_P, _P, _I64, _I32, _P, _P, _P]),
     "mck_group_create": (_ST, [ctypes.POINTER(_P), _P, _I32, _P, _I64, _I64, _I64, _I32]),
     "mck_group_set_grain": (_ST, [_P, _I32]),

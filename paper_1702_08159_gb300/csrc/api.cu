@@ -376,16 +376,17 @@ mck_status_t mck_features(mck_plan_t p, const float* x, int64_t n, int64_t in_di
 static mck_status_t run_backward(mck_plan_s* p, BackwardArgs b, cudaStream_t s, const char* who) {
   const int64_t n = b.f.n;
   if (n == 0) return MCK_OK;
-  const bool params = b.dCs || b.dG || b.phi_out;
+  const bool params = b.dCs || b.dG || b.dB || b.phi_out;
   const int64_t np = params ? backward_partials(p->L, n, p->E, p->num_sms) : 0;
   Scratch part(s);
-  MCK_TRY(part.alloc(sizeof(float) * (size_t)np * 2 * p->d));
+  MCK_TRY(part.alloc(sizeof(float) * (size_t)np * (b.dB ? 3 : 2) * p->d));
   return launched(launch_backward(b, (float*)part.ptr, np, s), who);
 }
 
-mck_status_t mck_features_backward(mck_plan_t p, const float* x, int64_t n, int64_t in_dim,
-                                   int64_t ldx, const float* Cs, const float* G, const float* dphi,
-                                   float* dx, float* dCs, float* dG, mck_stream_t stream) {
+mck_status_t mck_features_backward_ex(mck_plan_t p, const float* x, int64_t n, int64_t in_dim,
+                                      int64_t ldx, const float* Cs, const float* G,
+                                      const float* dphi, float* dx, float* dCs, float* dG,
+                                      float* dB, mck_stream_t stream) {
   MCK_TRY(check_plan(p));
   if (p->L < 5 || p->L > 10) return fail(MCK_EUNSUPPORTED, "the adjoint supports 32 <= d <= 1024");
   DeviceScope scope(p->device);
@@ -394,10 +395,12 @@ mck_status_t mck_features_backward(mck_plan_t p, const float* x, int64_t n, int6
   const int64_t F = 2 * p->E * p->d, tb = 4 * p->E * p->d;
   MCK_TRY(check_array(dCs, tb, p->device, "dCs", true));
   MCK_TRY(check_array(dG, tb, p->device, "dG", true));
+  MCK_TRY(check_array(dB, tb, p->device, "dB", true));
   if (n == 0) {  // sums over an empty batch are zero
     cudaError_t err = cudaSuccess;
     if (dCs) err = cudaMemsetAsync(dCs, 0, tb, (cudaStream_t)stream);
     if (dG && err == cudaSuccess) err = cudaMemsetAsync(dG, 0, tb, (cudaStream_t)stream);
+    if (dB && err == cudaSuccess) err = cudaMemsetAsync(dB, 0, tb, (cudaStream_t)stream);
     return launched(err, "mck_features_backward");
   }
   MCK_TRY(check_array(dphi, 4 * n * F, p->device, "dphi"));
@@ -409,7 +412,14 @@ mck_status_t mck_features_backward(mck_plan_t p, const float* x, int64_t n, int6
   b.dx = dx;
   b.dCs = dCs;
   b.dG = dG;
+  b.dB = dB;
   return run_backward(p, b, (cudaStream_t)stream, "mck_features_backward");
+}
+
+mck_status_t mck_features_backward(mck_plan_t p, const float* x, int64_t n, int64_t in_dim,
+                                   int64_t ldx, const float* Cs, const float* G, const float* dphi,
+                                   float* dx, float* dCs, float* dG, mck_stream_t stream) {
+  return mck_features_backward_ex(p, x, n, in_dim, ldx, Cs, G, dphi, dx, dCs, dG, nullptr, stream);
 }
 
 mck_status_t mck_fused_logits(mck_plan_t p, const float* x, int64_t n, int64_t in_dim, int64_t ldx,
@@ -435,10 +445,11 @@ mck_status_t mck_fused_logits(mck_plan_t p, const float* x, int64_t n, int64_t i
                   "mck_fused_logits");
 }
 
-mck_status_t mck_fused_logits_backward(mck_plan_t p, const float* x, int64_t n, int64_t in_dim,
-                                       int64_t ldx, const float* Cs, const float* G, const float* W,
-                                       int32_t C, const float* dlogits, float* dx, float* dCs,
-                                       float* dG, float* dW, float* db, mck_stream_t stream) {
+mck_status_t mck_fused_logits_backward_ex(mck_plan_t p, const float* x, int64_t n,
+                                          int64_t in_dim, int64_t ldx, const float* Cs,
+                                          const float* G, const float* W, int32_t C,
+                                          const float* dlogits, float* dx, float* dCs, float* dG,
+                                          float* dB, float* dW, float* db, mck_stream_t stream) {
   MCK_TRY(check_plan(p));
   if (p->L < 5 || p->L > 10) return fail(MCK_EUNSUPPORTED, "the adjoint supports 32 <= d <= 1024");
   if (C < 1 || C > MCK_MAX_CLASSES) return fail(MCK_EINVAL, "num_classes must be in [1, 16]");
@@ -450,6 +461,7 @@ mck_status_t mck_fused_logits_backward(mck_plan_t p, const float* x, int64_t n, 
   if ((uintptr_t)W % 16) return fail(MCK_EINVAL, "W must be 16-byte aligned");
   MCK_TRY(check_array(dCs, tb, p->device, "dCs", true));
   MCK_TRY(check_array(dG, tb, p->device, "dG", true));
+  MCK_TRY(check_array(dB, tb, p->device, "dB", true));
   MCK_TRY(check_array(dW, 4 * C * F, p->device, "dW", true));
   MCK_TRY(check_array(db, 4 * C, p->device, "db", true));
   cudaStream_t s = (cudaStream_t)stream;
@@ -458,6 +470,7 @@ mck_status_t mck_fused_logits_backward(mck_plan_t p, const float* x, int64_t n, 
     cudaError_t err = cudaSuccess;
     if (dCs) err = cudaMemsetAsync(dCs, 0, tb, s);
     if (dG && err == cudaSuccess) err = cudaMemsetAsync(dG, 0, tb, s);
+    if (dB && err == cudaSuccess) err = cudaMemsetAsync(dB, 0, tb, s);
     if (dW && err == cudaSuccess) err = cudaMemsetAsync(dW, 0, 4 * C * F, s);
     if (db && err == cudaSuccess) err = cudaMemsetAsync(db, 0, 4 * C, s);
     return launched(err, "mck_fused_logits_backward");
@@ -475,9 +488,25 @@ mck_status_t mck_fused_logits_backward(mck_plan_t p, const float* x, int64_t n, 
   b.dx = dx;
   b.dCs = dCs;
   b.dG = dG;
+  b.dB = dB;
   MCK_TRY(run_backward(p, b, s, "mck_fused_logits_backward"));
   return launched(launch_logit_weight_grads(dlogits, (const float*)phi.ptr, n, C, F, dW, db, s),
                   "mck_fused_logits_backward");
+}
+
+mck_status_t mck_fused_logits_backward(mck_plan_t p, const float* x, int64_t n, int64_t in_dim,
+                                       int64_t ldx, const float* Cs, const float* G, const float* W,
+                                       int32_t C, const float* dlogits, float* dx, float* dCs,
+                                       float* dG, float* dW, float* db, mck_stream_t stream) {
+  return mck_fused_logits_backward_ex(p, x, n, in_dim, ldx, Cs, G, W, C, dlogits, dx, dCs, dG,
+                                      nullptr, dW, db, stream);
+}
+
+mck_status_t mck_plan_set_signs(mck_plan_t p, const float* B, mck_stream_t stream) {
+  MCK_TRY(check_plan(p));
+  DeviceScope scope(p->device);
+  MCK_TRY(check_array(B, 4 * p->E * p->d, p->device, "B"));
+  return launched(set_signs(p, B, (cudaStream_t)stream), "mck_plan_set_signs");
 }
 
 mck_status_t mck_softmax_xent(const float* logits, const int32_t* labels, int64_t n, int32_t C,

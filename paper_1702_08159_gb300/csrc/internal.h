@@ -44,6 +44,9 @@ mck_status_t check_device_array(const void* p, int64_t bytes, int device, const 
 
 // ---- plan.cu -------------------------------------------------------------
 mck_status_t build_tables(mck_plan_s* p, cudaStream_t s);
+// Replace the plan's signs: B_e[k] = -1 where B[e][k] < 0 (device E x d
+// floats), and rebuild the lane-ordered tables that hold them (stream-ordered).
+cudaError_t set_signs(mck_plan_s* p, const float* B, cudaStream_t s);
 
 // ---- fwht.cu -------------------------------------------------------------
 cudaError_t launch_fwht(float* x, int64_t n, int L, int num_sms, cudaStream_t s);
@@ -94,10 +97,11 @@ struct BackwardArgs {
   float* dx;
   float* dCs;
   float* dG;
+  float* dB;  // optional E x d: gradient w.r.t. the diagonal B read as real values
 };
-// Partial rows of dCs/dG sums the adjoint writes: E x (blocks per expansion).
+// Partial rows of dCs/dG (and dB) sums the adjoint writes: E x (blocks per expansion).
 int64_t backward_partials(int L, int64_t n, int E, int num_sms);
-// partials: num_partials x 2 x d floats, num_partials = backward_partials(...).
+// partials: num_partials x (dB ? 3 : 2) x d floats, num_partials = backward_partials(...).
 cudaError_t launch_backward(const BackwardArgs& a, float* partials, int64_t num_partials,
                             cudaStream_t s);
 cudaError_t launch_logit_weight_grads(const float* dlogits, const float* phi, int64_t n, int C,

@@ -317,7 +317,48 @@ void launch_lane_tables(mck_plan_s* p, cudaStream_t s) {
                                                                      p->E);
 }
 
+// Signs from real values: bit k of word (e, k / 32) is set (B_e[k] = -1)
+// where B[e][k] < 0. One thread per word.
+__global__ void k_plan_set_signs(const float* __restrict__ B, uint32_t* __restrict__ bits,
+                                 int64_t d, int64_t words, int32_t E) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= words * E) return;
+  const int64_t e = t / words, w = t % words;
+  uint32_t m = 0;
+  for (int j = 0; j < 32; ++j) {
+    const int64_t k = w * 32 + j;
+    if (k < d && B[e * d + k] < 0.f) m |= 1u << j;
+  }
+  bits[t] = m;
+}
+
+// The lane-ordered copies of Pi, G and the B mask (warp and chunked kernels).
+cudaError_t launch_layout_tables(mck_plan_s* p, cudaStream_t s) {
+  if (!p->permB) return cudaSuccess;
+  switch (p->L) {
+    case 5: launch_lane_tables<5>(p, s); break;
+    case 6: launch_lane_tables<6>(p, s); break;
+    case 7: launch_lane_tables<7>(p, s); break;
+    case 8: launch_lane_tables<8>(p, s); break;
+    case 9: launch_lane_tables<9>(p, s); break;
+    case 10: launch_lane_tables<10>(p, s); break;
+    case 11: launch_chunk_tables<11>(p, s); break;
+    case 12: launch_chunk_tables<12>(p, s); break;
+    case 13: launch_chunk_tables<13>(p, s); break;
+    case 14: launch_chunk_tables<14>(p, s); break;
+    default: break;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t set_signs(mck_plan_s* p, const float* B, cudaStream_t s) {
+  k_plan_set_signs<<<blocks_for(p->words * p->E, 128), 128, 0, s>>>(B, p->B_bits, p->d, p->words,
+                                                                   p->E);
+  const cudaError_t err = cudaGetLastError();
+  return err != cudaSuccess ? err : launch_layout_tables(p, s);
+}
 
 mck_status_t build_tables(mck_plan_s* p, cudaStream_t s) {
   const uint32_t k0 = (uint32_t)(p->seed & 0xffffffffu), k1 = (uint32_t)(p->seed >> 32);
@@ -355,22 +396,7 @@ mck_status_t build_tables(mck_plan_s* p, cudaStream_t s) {
     k_plan_perm<<<(unsigned)E, 1024, perm_smem, s>>>(p->perm, d, k0, k1);
     err = cudaGetLastError();
   }
-  if (err == cudaSuccess && p->permB) {
-    switch (p->L) {
-      case 5: launch_lane_tables<5>(p, s); break;
-      case 6: launch_lane_tables<6>(p, s); break;
-      case 7: launch_lane_tables<7>(p, s); break;
-      case 8: launch_lane_tables<8>(p, s); break;
-      case 9: launch_lane_tables<9>(p, s); break;
-      case 10: launch_lane_tables<10>(p, s); break;
-      case 11: launch_chunk_tables<11>(p, s); break;
-      case 12: launch_chunk_tables<12>(p, s); break;
-      case 13: launch_chunk_tables<13>(p, s); break;
-      case 14: launch_chunk_tables<14>(p, s); break;
-      default: break;
-    }
-    err = cudaGetLastError();
-  }
+  if (err == cudaSuccess) err = launch_layout_tables(p, s);
   cudaFreeAsync(G64, s);
   cudaFreeAsync(norm, s);
   if (err != cudaSuccess) return cuda_fail(err, "plan kernels");

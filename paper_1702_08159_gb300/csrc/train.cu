@@ -10,13 +10,14 @@
 //   dCs += h dz            dh = Cs dz         dw = H dh
 //   dG  += v dw            dv = G dw          du[pi(k)] = dv[k]      du0 = H du
 //   dx  += (B du0)[:in_dim]
+//   dB  += x-hat du0       (B read as a real diagonal; optional)
 // Two kernels share that per-sample core:
 //   k_bwd_params  a block of 8 warps per (expansion, range of samples): G_e,
 //                 Cs_e (and, fused, W_e or the block's dphi rows) staged in
-//                 shared memory; per-warp running sums of h dz and v dw,
-//                 added over the warps in order into one partial row per
-//                 block; k_reduce_params sums the rows of each expansion in
-//                 order.
+//                 shared memory; per-warp running sums of h dz and v dw
+//                 (and x-hat B du0 for dB), added over the warps in order
+//                 into one partial row per block; k_reduce_params sums the
+//                 rows of each expansion in order.
 //   k_bwd_input   each warp owns samples and loops over all expansions,
 //                 accumulating dx in registers (no cross-warp sum needed).
 // With fused logits the upstream gradient is dphi = W^T dlogits, formed
@@ -194,6 +195,34 @@ __device__ __forceinline__ void load_G_B(const FeatureArgs& a, const BwdTabs& tb
   }
 }
 
+// x-hat of sample n in layout A (zero past in_dim, and for an invalid sample).
+template <int L>
+__device__ __forceinline__ void load_x_A(const BwdLaunch& P, int64_t n, bool valid, int lam,
+                                         float (&w)[32]) {
+  using Y = Lay<L>;
+  const FeatureArgs& a = P.b.f;
+  const float* row = a.x + n * a.ldx;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int k0 = Y::kA(lam, 4 * m);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+      if (P.vec_x) {
+        if (k0 < a.in_dim) v = __ldg(reinterpret_cast<const float4*>(row + k0));
+      } else {
+        if (k0 + 0 < a.in_dim) v.x = __ldg(row + k0 + 0);
+        if (k0 + 1 < a.in_dim) v.y = __ldg(row + k0 + 1);
+        if (k0 + 2 < a.in_dim) v.z = __ldg(row + k0 + 2);
+        if (k0 + 3 < a.in_dim) v.w = __ldg(row + k0 + 3);
+      }
+    }
+    w[4 * m] = v.x;
+    w[4 * m + 1] = v.y;
+    w[4 * m + 2] = v.z;
+    w[4 * m + 3] = v.w;
+  }
+}
+
 // One sample of one expansion: forward recompute and backward. On return w
 // holds B du0 (layout A), the sample's contribution to dx-hat.
 template <int L, bool FUSED, bool PARAMS>
@@ -209,28 +238,7 @@ __device__ __forceinline__ void bwd_core(const BwdLaunch& P, const BwdTabs& tb, 
   const int lane = threadIdx.x & 31;
   float* buf = S.buf;
   // ---- forward: u = H B x-hat, v = Pi u, h = H G v ----
-  {
-    const float* row = a.x + n * a.ldx;
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int k0 = Y::kA(lam, 4 * m);
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (valid) {
-        if (P.vec_x) {
-          if (k0 < a.in_dim) v = __ldg(reinterpret_cast<const float4*>(row + k0));
-        } else {
-          if (k0 + 0 < a.in_dim) v.x = __ldg(row + k0 + 0);
-          if (k0 + 1 < a.in_dim) v.y = __ldg(row + k0 + 1);
-          if (k0 + 2 < a.in_dim) v.z = __ldg(row + k0 + 2);
-          if (k0 + 3 < a.in_dim) v.w = __ldg(row + k0 + 3);
-        }
-      }
-      w[4 * m] = v.x;
-      w[4 * m + 1] = v.y;
-      w[4 * m + 2] = v.z;
-      w[4 * m + 3] = v.w;
-    }
-  }
+  load_x_A<L>(P, n, valid, lam, w);
   apply_signs(w, bmask);
   hreg<Y::maskA()>(w);
   if constexpr (L > 5) {
@@ -404,21 +412,43 @@ __device__ __forceinline__ void bwd_core(const BwdLaunch& P, const BwdTabs& tb, 
 // order and the block writes one partial row (E x bpe rows in all).
 constexpr int kBP = 8;  // warps per block of k_bwd_params
 
-template <int L>
+template <int L, bool DB>
 struct BwdBlockSmem {
   alignas(16) float gl[32 * 32];
   alignas(16) float csl[32 * 32];
   BwdSmem<L, true> warp[kBP];
+  alignas(16) float db[DB ? kBP * 32 * 32 : 4];  // per-warp running sums of x-hat B du0, layout A
   // followed by W_e (C x 2d floats) when staged
 };
 
-template <int L, bool FUSED>
+// dB: x-hat (B du0) of the sample just processed, added to the warp's sums
+// (B is applied once, when the block writes its row: x-hat du0 = B x-hat (B du0)).
+template <int L>
+__device__ __forceinline__ void add_db(const BwdLaunch& P, int64_t n, bool valid, int lam,
+                                       float* dbw, const float (&w)[32]) {
+  const int lane = threadIdx.x & 31;
+  float xv[32];
+  load_x_A<L>(P, n, valid, lam, xv);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    float4& acc = lane4(dbw, m, lane);
+    float4 t = acc;
+    t.x = fmaf(xv[4 * m], w[4 * m], t.x);
+    t.y = fmaf(xv[4 * m + 1], w[4 * m + 1], t.y);
+    t.z = fmaf(xv[4 * m + 2], w[4 * m + 2], t.z);
+    t.w = fmaf(xv[4 * m + 3], w[4 * m + 3], t.w);
+    acc = t;
+  }
+}
+
+template <int L, bool FUSED, bool DB>
 __global__ void __launch_bounds__(kBP * 32, 1) k_bwd_params(const BwdLaunch P) {
   using Y = Lay<L>;
   using BS = BShape<L>;
   constexpr int d = Y::d;
+  constexpr int rows = DB ? 3 : 2;  // partial rows per block: dCs, dG (, dB)
   extern __shared__ float4 sm4[];
-  BwdBlockSmem<L>& B = *reinterpret_cast<BwdBlockSmem<L>*>(sm4);
+  BwdBlockSmem<L, DB>& B = *reinterpret_cast<BwdBlockSmem<L, DB>*>(sm4);
   float* Wsm = reinterpret_cast<float*>(&B + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   BwdSmem<L, true>& S = B.warp[warp];
@@ -452,10 +482,12 @@ __global__ void __launch_bounds__(kBP * 32, 1) k_bwd_params(const BwdLaunch P) {
   uint32_t bmask;
   uint32_t poff[16];
   load_tables<L>(a, e, lam, bmask, poff);
+  float* dbw = B.db + (DB ? warp * 32 * 32 : 0);
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     lane4(S.dcs, m, lane) = make_float4(0.f, 0.f, 0.f, 0.f);
     lane4(S.dg, m, lane) = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (DB) lane4(dbw, m, lane) = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();
   if constexpr (FUSED && L == 10) {
@@ -511,6 +543,7 @@ __global__ void __launch_bounds__(kBP * 32, 1) k_bwd_params(const BwdLaunch P) {
         float w[32];
         // a row past the block's range has x-hat = 0 and dphi = 0: it adds nothing
         bwd_core<L, FUSED, true>(P, tb, n, e, n < n1, g, lam, S, slot, bmask, poff, w);
+        if constexpr (DB) add_db<L>(P, n, n < n1, lam, dbw, w);
       }
     }
   }
@@ -525,6 +558,7 @@ __global__ void __launch_bounds__(kBP * 32, 1) k_bwd_params(const BwdLaunch P) {
       // An invalid sample contributes exactly zero: x-hat = 0 gives h = 0,
       // and its upstream gradient is read as 0 (dphi) or dlogits = 0.
       bwd_core<L, FUSED, true>(P, tb, n, e, valid, g, lam, S, slot, bmask, poff, w);
+      if constexpr (DB) add_db<L>(P, n, valid, lam, dbw, w);
     }
   }
   // Sum the warp's sample groups (lanes with equal lam) into lanes of group 0,
@@ -533,27 +567,31 @@ __global__ void __launch_bounds__(kBP * 32, 1) k_bwd_params(const BwdLaunch P) {
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
     const int at = ((j >> 2) * 32 + lane) * 4 + (j & 3);
-    float s1 = S.dcs[at], s2 = S.dg[at];
+    float s1 = S.dcs[at], s2 = S.dg[at], s3 = DB ? dbw[at] : 0.f;
 #pragma unroll
     for (int o = Y::T; o < 32; o <<= 1) {
       s1 += __shfl_xor_sync(0xffffffffu, s1, o);
       s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      if constexpr (DB) s3 += __shfl_xor_sync(0xffffffffu, s3, o);
     }
     S.dcs[at] = s1;
     S.dg[at] = s2;
+    if constexpr (DB) dbw[at] = s3;
   }
   __syncthreads();
-  float* pr = P.partials + ((int64_t)e * P.bpe + sb) * 2 * d;
+  float* pr = P.partials + ((int64_t)e * P.bpe + sb) * rows * d;
   for (int j = warp; j < 32; j += kBP) {
     const int at = ((j >> 2) * 32 + lane) * 4 + (j & 3);
-    float s1 = 0.f, s2 = 0.f;
+    float s1 = 0.f, s2 = 0.f, s3 = 0.f;
     for (int w2 = 0; w2 < kBP; ++w2) {
       s1 += B.warp[w2].dcs[at];
       s2 += B.warp[w2].dg[at];
+      if constexpr (DB) s3 += B.db[w2 * 32 * 32 + at];
     }
     if (g == 0) {
       pr[Y::kA(lam, j)] = s1;
       pr[d + Y::kB(lam, j)] = s2;
+      if constexpr (DB) pr[2 * d + Y::kA(lam, j)] = ((bmask >> j) & 1u) ? -s3 : s3;
     }
   }
 }
@@ -597,40 +635,42 @@ __global__ void __launch_bounds__(kBW * 32, kBwdInputMinBlocks) k_bwd_input(cons
   }
 }
 
-// dCs[e][k] = sum over the expansion's partial rows of row 0; dG likewise row 1.
-// A block owns 64 consecutive k of one expansion: thread (qg, c4) adds the
-// partial rows q = qg, qg + 16, ... of float4 column c4 in order, and the 16
-// groups are then added in order through shared memory.
+// dCs[e][k] = sum over the expansion's partial rows of row 0; dG likewise
+// row 1, and dB row 2 (rows = 3). A block owns 64 consecutive k of one
+// expansion: thread (qg, c4) adds the partial rows q = qg, qg + 16, ... of
+// float4 column c4 in order, and the 16 groups are then added in order
+// through shared memory.
 constexpr int kRpCols = 16, kRpGroups = 16;  // float4 columns x row groups per block
 
 __global__ void __launch_bounds__(kRpCols * kRpGroups) k_reduce_params(
-    const float* __restrict__ partials, int64_t d, int E, int rpe, float* __restrict__ dCs,
-    float* __restrict__ dG) {
-  __shared__ float4 red[2][kRpGroups][kRpCols];
+    const float* __restrict__ partials, int64_t d, int E, int rpe, int rows,
+    float* __restrict__ dCs, float* __restrict__ dG, float* __restrict__ dB) {
+  __shared__ float4 red[3][kRpGroups][kRpCols];
   const int c4 = threadIdx.x % kRpCols, qg = threadIdx.x / kRpCols;
   const int cols = d / 4 < kRpCols ? (int)(d / 4) : kRpCols;  // d = 32 has 8 float4 columns
   const int64_t blocks_per_e = d / (4 * cols);
   const int64_t e = blockIdx.x / blocks_per_e;
   const int64_t k = (blockIdx.x % blocks_per_e) * 4 * cols + 4 * c4;
   const bool on = c4 < cols;
-  const float4* base = reinterpret_cast<const float4*>(partials + e * rpe * 2 * d + k);
-  const int64_t stride = 2 * d / 4;  // float4s between consecutive partial rows
-  float4 s1 = make_float4(0.f, 0.f, 0.f, 0.f), s2 = s1;
+  const float4* base = reinterpret_cast<const float4*>(partials + e * rpe * rows * d + k);
+  const int64_t stride = rows * d / 4;  // float4s between consecutive partial rows
+  float4 s[3];
+  for (int r = 0; r < 3; ++r) s[r] = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int q = qg; on && q < rpe; q += kRpGroups) {
-    const float4 a = __ldg(base + q * stride), b = __ldg(base + q * stride + d / 4);
-    s1.x += a.x; s1.y += a.y; s1.z += a.z; s1.w += a.w;
-    s2.x += b.x; s2.y += b.y; s2.z += b.z; s2.w += b.w;
+    for (int r = 0; r < rows; ++r) {
+      const float4 a = __ldg(base + q * stride + r * (d / 4));
+      s[r].x += a.x; s[r].y += a.y; s[r].z += a.z; s[r].w += a.w;
+    }
   }
-  red[0][qg][c4] = s1;
-  red[1][qg][c4] = s2;
+  for (int r = 0; r < 3; ++r) red[r][qg][c4] = s[r];
   __syncthreads();
-  if (qg < 2 && on) {  // group 0 finishes dCs, group 1 dG
+  if (qg < rows && on) {  // group 0 finishes dCs, group 1 dG, group 2 dB
     float4 t = red[qg][0][c4];
     for (int q = 1; q < kRpGroups; ++q) {
       const float4 v = red[qg][q][c4];
       t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w;
     }
-    float* o = qg == 0 ? dCs : dG;  // may be only 4-byte aligned
+    float* o = qg == 0 ? dCs : (qg == 1 ? dG : dB);  // may be only 4-byte aligned
     if (o) {
       o += e * d + k;
       o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
@@ -795,37 +835,46 @@ cudaError_t run_weight_grads(const float* dlogits, const float* phi, int64_t n, 
   return cudaGetLastError();
 }
 
+template <int L, bool FUSED, bool DB>
+cudaError_t run_params(BwdLaunch& P, int64_t num_partials, cudaStream_t s) {
+  const FeatureArgs& a = P.b.f;
+  size_t smem_p = sizeof(BwdBlockSmem<L, DB>);
+  const size_t wbytes = FUSED ? sizeof(float) * (size_t)P.b.C * 2 * ((size_t)1 << L) : 0;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    optin = 0;
+  const size_t tbytes = sizeof(float) * (size_t)kBP * (2 * ((size_t)1 << L) + CMAX);
+  P.d_tile = FUSED && L == 10 && smem_p + tbytes <= (size_t)optin;
+  P.w_smem = FUSED && !P.d_tile && smem_p + wbytes <= (size_t)optin;
+  if (P.d_tile) smem_p += tbytes;
+  else if (P.w_smem) smem_p += wbytes;
+  cudaError_t err = cudaFuncSetAttribute(k_bwd_params<L, FUSED, DB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p);
+  if (err != cudaSuccess) return err;
+  P.bpe = (int)(num_partials / a.E);
+  k_bwd_params<L, FUSED, DB><<<(unsigned)num_partials, kBP * 32, smem_p, s>>>(P);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  if (P.b.dCs || P.b.dG || DB) {
+    const int cols = std::min(kRpCols, (1 << L) / 4);
+    const unsigned blocks = (unsigned)(((int64_t)a.E << L) / (4 * cols));
+    k_reduce_params<<<blocks, kRpCols * kRpGroups, 0, s>>>(
+        P.partials, (int64_t)1 << L, a.E, P.bpe, DB ? 3 : 2, P.b.dCs, P.b.dG, P.b.dB);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
+
 template <int L, bool FUSED>
 cudaError_t run_bwd(const BwdLaunch& P0, int64_t num_partials, cudaStream_t s) {
   BwdLaunch P = P0;
   const FeatureArgs& a = P.b.f;
   const size_t smem_i = sizeof(BwdSmem<L, false>) * kBW;
   cudaError_t err;
-  if (P.b.dCs || P.b.dG || P.b.phi_out) {
-    size_t smem_p = sizeof(BwdBlockSmem<L>);
-    const size_t wbytes = FUSED ? sizeof(float) * (size_t)P.b.C * 2 * ((size_t)1 << L) : 0;
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-      optin = 0;
-    const size_t tbytes = sizeof(float) * (size_t)kBP * (2 * ((size_t)1 << L) + CMAX);
-    P.d_tile = FUSED && L == 10 && smem_p + tbytes <= (size_t)optin;
-    P.w_smem = FUSED && !P.d_tile && smem_p + wbytes <= (size_t)optin;
-    if (P.d_tile) smem_p += tbytes;
-    else if (P.w_smem) smem_p += wbytes;
-    err = cudaFuncSetAttribute(k_bwd_params<L, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem_p);
+  if (P.b.dCs || P.b.dG || P.b.dB || P.b.phi_out) {
+    err = P.b.dB ? run_params<L, FUSED, true>(P, num_partials, s)
+                 : run_params<L, FUSED, false>(P, num_partials, s);
     if (err != cudaSuccess) return err;
-    P.bpe = (int)(num_partials / a.E);
-    k_bwd_params<L, FUSED><<<(unsigned)num_partials, kBP * 32, smem_p, s>>>(P);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    if (P.b.dCs || P.b.dG) {
-      const int cols = std::min(kRpCols, (1 << L) / 4);
-      const unsigned blocks = (unsigned)(((int64_t)a.E << L) / (4 * cols));
-      k_reduce_params<<<blocks, kRpCols * kRpGroups, 0, s>>>(
-          P.partials, (int64_t)1 << L, a.E, P.bpe, P.b.dCs, P.b.dG);
-      if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    }
   }
   if (P.b.dx) {
     err = cudaFuncSetAttribute(k_bwd_input<L, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -61,6 +61,17 @@ def test_grads_against_central_differences(problem):
     _check(g["dCs"].ravel(), tr.finite_difference(f, T["Cs"], range(T["Cs"].size)))
     _check(g["dG"].ravel(), tr.finite_difference(f, T["G"], range(T["G"].size)))
     _check(g["dx"].ravel()[idx_x], tr.finite_difference(f, x, idx_x))
+    # B as a real diagonal (u0 = B x-hat): the loss is smooth in it
+    T["B"] = T["B"].astype(np.float64)
+    _check(g["dB"].ravel(), tr.finite_difference(f, T["B"], range(T["B"].size)))
+
+
+def test_sign_gradient_zero_past_input(problem):
+    # Coordinates k >= in_dim of x-hat are zero padding: B has no effect there.
+    T, x, W, b, y = problem
+    g = tr.train_grads(x, T, W, b, y)
+    assert np.all(g["dB"][:, x.shape[1]:] == 0.0)
+    assert np.abs(g["dB"][:, : x.shape[1]]).max() > 0
 
 
 def test_features_backward_is_adjoint(problem):
