@@ -148,6 +148,22 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// 16-byte asynchronous copy from global to shared memory, cached in L2 only.
+// With bytes < 16 the rest of the destination is zero-filled (bytes = 0
+// reads nothing). Completion is tracked per thread by commit groups.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+// Wait until at most N of this thread's most recent commit groups are pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ void sts32(uint32_t addr, float v) {
   asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
@@ -286,14 +302,22 @@ __device__ __forceinline__ void chunk_columns_inplace(float* sm, int tid) {
 // when the caller overrides it; the B masks per (chunk, lane); Cs natural.
 // `out` receives [cos z | sin z] (2d floats). `bar` synchronises the NT
 // threads of the (sub-)block.
-template <int L, class Bar>
-__device__ __forceinline__ void chunked_map(const float* __restrict__ xrow, int64_t in_dim,
-                                            bool vec_x, const uint32_t* __restrict__ permB,
-                                            const float* __restrict__ GB,
-                                            const float* __restrict__ Gnat,
-                                            const uint32_t* __restrict__ maskA,
-                                            const float* __restrict__ cs, float* __restrict__ out,
-                                            float* sm, int tid, Bar bar) {
+// STAGED: the caller has copied x-hat into shared memory with cp.async (xs:
+// this warp's 1024-float chunk, zero past in_dim, in one commit group that
+// it has waited for) and Cs (css: the expansion's d values, in the commit
+// group before the one `next` makes). The warp reads its chunk, then calls
+// `next` (which queues the next item's copies into xs); the output stage
+// waits for the Cs group.
+template <int L, bool STAGED, class Bar, class Next>
+__device__ __forceinline__ void chunked_map_impl(const float* __restrict__ xrow, int64_t in_dim,
+                                                 bool vec_x, const uint32_t* __restrict__ permB,
+                                                 const float* __restrict__ GB,
+                                                 const float* __restrict__ Gnat,
+                                                 const uint32_t* __restrict__ maskA,
+                                                 const float* __restrict__ cs,
+                                                 float* __restrict__ out, float* sm, int tid,
+                                                 Bar bar, const float* xs, const float* css,
+                                                 Next next) {
   using C = Chunked<L>;
   using Y = Lay<10>;
   constexpr int d = 1 << L;
@@ -330,22 +354,36 @@ __device__ __forceinline__ void chunked_map(const float* __restrict__ xrow, int6
   // u = H B x-hat: index bits 0..9 per warp, then 10..L-1 across the chunks
   {
     float w[32];
+    if constexpr (STAGED) {
+      __syncwarp();  // every lane has waited for its own copies of the chunk
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int k0 = co + Y::kA(lane, 4 * m);
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (vec_x) {
-        if (k0 < in_dim) v = __ldg(reinterpret_cast<const float4*>(xrow + k0));
-      } else {
-        if (k0 + 0 < in_dim) v.x = __ldg(xrow + k0 + 0);
-        if (k0 + 1 < in_dim) v.y = __ldg(xrow + k0 + 1);
-        if (k0 + 2 < in_dim) v.z = __ldg(xrow + k0 + 2);
-        if (k0 + 3 < in_dim) v.w = __ldg(xrow + k0 + 3);
+      for (int m = 0; m < 8; ++m) {
+        const float4 v = *reinterpret_cast<const float4*>(xs + Y::kA(lane, 4 * m));
+        w[4 * m] = v.x;
+        w[4 * m + 1] = v.y;
+        w[4 * m + 2] = v.z;
+        w[4 * m + 3] = v.w;
       }
-      w[4 * m] = v.x;
-      w[4 * m + 1] = v.y;
-      w[4 * m + 2] = v.z;
-      w[4 * m + 3] = v.w;
+      __syncwarp();  // the chunk is read before the next item's copies land
+      next();
+    } else {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int k0 = co + Y::kA(lane, 4 * m);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (vec_x) {
+          if (k0 < in_dim) v = __ldg(reinterpret_cast<const float4*>(xrow + k0));
+        } else {
+          if (k0 + 0 < in_dim) v.x = __ldg(xrow + k0 + 0);
+          if (k0 + 1 < in_dim) v.y = __ldg(xrow + k0 + 1);
+          if (k0 + 2 < in_dim) v.z = __ldg(xrow + k0 + 2);
+          if (k0 + 3 < in_dim) v.w = __ldg(xrow + k0 + 3);
+        }
+        w[4 * m] = v.x;
+        w[4 * m + 1] = v.y;
+        w[4 * m + 2] = v.z;
+        w[4 * m + 3] = v.w;
+      }
     }
 #pragma unroll
     for (int j = 0; j < 32; ++j)
@@ -374,6 +412,7 @@ __device__ __forceinline__ void chunked_map(const float* __restrict__ xrow, int6
   hreg<Y::maskA()>(w);
   __syncwarp();
   store_A<10>(slot, 0, lane, w);
+  if constexpr (STAGED) cp_async_wait<1>();  // this thread's Cs copies have landed
   bar();
   // bits 10..L-1 of the second transform, then z = Cs h and [cos | sin]
 #pragma unroll
@@ -397,7 +436,8 @@ __device__ __forceinline__ void chunked_map(const float* __restrict__ xrow, int6
     for (int i = 0; i < C::W; ++i) {
       const int k = c0 + 1024 * i;
       float cv[C::VEC], cz[C::VEC], sz[C::VEC];
-      ld_vec<C::VEC>(cs + k, cv);
+      if constexpr (STAGED) ld_vec<C::VEC>(css + k, cv);
+      else ld_vec<C::VEC>(cs + k, cv);
 #pragma unroll
       for (int v = 0; v < C::VEC; ++v) cos_sin(cv[v] * u[i][v], cz[v], sz[v]);
       if constexpr (C::VEC == 4) {
@@ -409,7 +449,19 @@ __device__ __forceinline__ void chunked_map(const float* __restrict__ xrow, int6
       }
     }
   }
-  bar();  // the slots are read before the next item rewrites them
+  bar();  // the slots (and Cs) are read before the next item rewrites them
+}
+
+template <int L, class Bar>
+__device__ __forceinline__ void chunked_map(const float* __restrict__ xrow, int64_t in_dim,
+                                            bool vec_x, const uint32_t* __restrict__ permB,
+                                            const float* __restrict__ GB,
+                                            const float* __restrict__ Gnat,
+                                            const uint32_t* __restrict__ maskA,
+                                            const float* __restrict__ cs, float* __restrict__ out,
+                                            float* sm, int tid, Bar bar) {
+  chunked_map_impl<L, false>(xrow, in_dim, vec_x, permB, GB, Gnat, maskA, cs, out, sm, tid, bar,
+                             nullptr, nullptr, [] {});
 }
 
 }  // namespace mck

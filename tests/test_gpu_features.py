@@ -53,6 +53,21 @@ def test_all_sizes(mck, dev, L):
     assert _max_err(phi, ref) <= TOL
 
 
+@pytest.mark.parametrize("d,E,n,in_dim", [(2048, 3, 120, 1500), (16384, 2, 200, 12288),
+                                          (16384, 3, 61, 16384)])
+def test_chunked_blocks_take_several_items(mck, dev, d, E, n, in_dim):
+    """More items than blocks, so every block runs several (row, expansion)
+    items in turn; at d = 2^14 with 16-byte rows this is the staged kernel,
+    which copies the next item's input and the current item's Cs into shared
+    memory while the block works (zero-filled past in_dim)."""
+    plan = mck.Plan(d, E, "rbf", 2.0, 4242 + d)
+    x = (wl.gaussian(n, in_dim, seed=n) * np.float32(6 * 2.0 / np.sqrt(in_dim))).astype(np.float32)
+    phi = mck.features(plan, torch.from_numpy(x).to(dev)).cpu().numpy()
+    ref = ff.features(x.astype(np.float64), _oracle_tables(plan))
+    assert _max_err(phi, ref) <= TOL
+    plan.close()
+
+
 @pytest.mark.parametrize("in_dim", [1, 3, 783, 784, 1024])
 def test_ragged_input_dims(mck, dev, in_dim):
     plan = mck.Plan(1024, 2, "rbf", 1.0, 5)
