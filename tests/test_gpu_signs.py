@@ -37,6 +37,18 @@ def _rel(got, ref):
     return float(np.abs(got.astype(np.float64) - ref).max() / max(np.abs(ref).max(), 1e-30))
 
 
+def _phase_tol(z, Cs, d):
+    """Per-feature bound of a float32 feature against the float64 oracle run
+    on the same float32 Cs, (n, 2 E d): 1e-5 plus float32's resolution of the
+    phase and the transform's rounding, 2^-24 (|z_k| + 4 log2(d) Cs_k max|h|).
+    Needed for Laplacian plans, whose heavy-tailed radii give a few large
+    phases; capped at 2 (any value in [-1, 1] passes)."""
+    Cs = Cs[None]
+    hmax = np.abs(z / Cs).max(axis=2, keepdims=True)
+    t = 1e-5 + 2.0 ** -24 * (np.abs(z) + 4 * np.log2(d) * Cs * hmax)
+    return np.minimum(np.concatenate([t, t], axis=2).reshape(z.shape[0], -1), 2.0)
+
+
 def _latent(E, d, seed):
     g = np.random.default_rng(seed)
     B = g.standard_normal((E, d)).astype(np.float32)
@@ -150,4 +162,62 @@ def test_classifier_straight_through_signs(mck, dev):
         model.Br.copy_(-model.Br)
     model(torch.from_numpy(x[:2]).to(dev))
     np.testing.assert_array_equal(plan.signs(), np.where(-Bl < 0, -1.0, 1.0))
+    plan.close()
+
+
+def test_group_sees_new_signs_and_laplace_plans(mck, dev):
+    """A group built before mck_plan_set_signs uses the new signs (it reads the
+    plans' tables at launch), including the lane and chunk masks of its warp
+    steps and block items; one of the plans has the Laplacian calibration."""
+    specs = [(64, "rbf"), (1024, "laplace"), (4096, "rbf")]
+    plans = [mck.Plan(d, 3, k, 3.0, 99) for d, k in specs]
+    Bs = [_latent(3, d, seed=500 + d) for d, _ in specs]
+    E = [3, 2, 3, 1, 2, 3]
+    pidx = [0, 1, 2, 0, 1, 2]
+    in_dims = [64, 784, 4000, 60, 1024, 4096]
+    items, x_len, phi_len = mck.group_layout(plans, pidx, E, in_dims)
+    xh = np.zeros(x_len, np.float32)
+    xs = []
+    for i, n in enumerate(in_dims):
+        v = (wl.gaussian(1, n, seed=i)[0] * np.float32(6.0 / np.sqrt(n))).astype(np.float32)
+        xh[items["x_offset"][i]: items["x_offset"][i] + n] = v
+        xs.append(v)
+    group = mck.Group(plans, items, x_len, phi_len)
+    for p, B in zip(plans, Bs):
+        p.set_signs(torch.from_numpy(B).to(dev))
+    x = torch.from_numpy(xh).to(dev)
+    phi = torch.full((phi_len,), float("nan"), device=dev)
+    group.features(x, phi)
+    got = phi.cpu().numpy().astype(np.float64)
+    for i, (p, e, n) in enumerate(zip(pidx, E, in_dims)):
+        plan = plans[p]
+        T = dict(_tables(plan, Bs[p]), Cs=plan.tables()["Cs"].astype(np.float64))
+        Te = {k: (v[:e] if isinstance(v, np.ndarray) else v) for k, v in T.items()}
+        xi = xs[i][None].astype(np.float64)
+        ref = ff.features(xi, Te)[0]
+        tol = _phase_tol(ff.phases(xi, Te), Te["Cs"], plan.d)[0]
+        o = int(items["phi_offset"][i])
+        assert np.all(np.abs(got[o: o + 2 * e * plan.d] - ref) <= tol), i
+    for p in plans:
+        p.close()
+
+
+def test_laplace_fused_logits(mck, dev):
+    plan = mck.Plan(1024, 4, "laplace", 3.0, 31)
+    x = wl.mnist_like(40, 784, seed=3)
+    W, _ = wl.logit_weights(10, plan.num_features, seed=2, std=0.05)
+    b = np.linspace(-1, 1, 10).astype(np.float32)
+    got = mck.fused_logits(plan, torch.from_numpy(x).to(dev), torch.from_numpy(W).to(dev),
+                           torch.from_numpy(b).to(dev)).cpu().numpy()
+    # The oracle on the plan's own float32 Cs. Laplacian radii are heavy tailed,
+    # so a few phases are large: each feature's float32 error is bounded as in
+    # the Laplacian feature test, 2^-24 (|z_k| + 4 log2(d) Cs_k max_j |h_j|),
+    # and the logits bar adds those bounds weighted by |W|.
+    T = dict(_tables(plan), Cs=plan.tables()["Cs"].astype(np.float64))
+    ft = _phase_tol(ff.phases(x.astype(np.float64), T), T["Cs"], plan.d)
+    bar = 1e-4 + ft @ np.abs(W.astype(np.float64)).T
+    ref = tr.logits(ff.features(x.astype(np.float64), T), W.astype(np.float64),
+                    b.astype(np.float64))
+    assert np.all(np.abs(got - ref) <= bar)
+    assert np.abs(got - ref).max() <= 1e-3
     plan.close()
