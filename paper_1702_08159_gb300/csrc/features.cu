@@ -142,6 +142,49 @@ __device__ __forceinline__ void epilogue_A(const Launch& P, int64_t n, int e, bo
   }
 }
 
+// Features at d = 32 and 64 (one or two lanes per vector): a lane's 16-byte
+// pieces of one row are 2 E d floats away from its neighbours' rows, so the
+// warp first lays its VPW rows of cos and of sin out in shared memory (row
+// stride d + 4T words: conflict-free for the 128-bit stores of layout A) and
+// then writes them back row by row, each instruction covering 512 contiguous
+// bytes of one or more rows (128-byte segments at d = 32).
+constexpr int kRowsBuf = 2 * 1152;  // cos and sin rows: 2 x VPW (d + 4T) floats
+
+template <int L>
+__device__ __forceinline__ void epilogue_rows(const Launch& P, int64_t n0, int e, int g, int lam,
+                                              const float (&h)[32], const float (&cs)[32],
+                                              float* buf) {
+  using Y = Lay<L>;
+  constexpr int d = Y::d, RS = d + 4 * Y::T, HALF = (32 / Y::T) * RS;
+  static_assert(2 * HALF <= kRowsBuf, "row buffer");
+  const int lane = threadIdx.x & 31;
+  const int64_t F = 2ll * P.a.E * d;
+  __syncwarp();  // every lane is done with the buffer's previous contents
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    float c[4], s4[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cos_sin(cs[4 * m + q] * h[4 * m + q], c[q], s4[q]);
+    const int at = g * RS + Y::kA(lam, 4 * m);
+    *reinterpret_cast<float4*>(buf + at) = make_float4(c[0], c[1], c[2], c[3]);
+    *reinterpret_cast<float4*>(buf + HALF + at) = make_float4(s4[0], s4[1], s4[2], s4[3]);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int f = 128 * i + 4 * lane;  // element of the warp's VPW x d block
+    const int r = f / d, col = f % d;
+    const int64_t n = n0 + r;
+    if (n < P.a.n) {
+      float* o = P.phi + n * F + 2ll * e * d + col;
+      __stcs(reinterpret_cast<float4*>(o), *reinterpret_cast<const float4*>(buf + r * RS + col));
+      __stcs(reinterpret_cast<float4*>(o + d),
+             *reinterpret_cast<const float4*>(buf + HALF + r * RS + col));
+    }
+  }
+  __syncwarp();  // the rows are read before the buffer is reused
+}
+
 // ---------------------------------------------------------------------------
 // Warp kernel, 5 <= L <= 10.
 // ---------------------------------------------------------------------------
@@ -162,7 +205,11 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_FEATURES ? kWarpMinB
   using Y = Lay<L>;
   using WS = WarpShape<L>;
   constexpr int d = Y::d;
-  __shared__ __align__(16) float sm[kWarps][WS::VPW * Y::SLOT];
+  // Row-wise output stores at d = 32 and 64 (feature sweep: 0.746 -> 0.337 ms
+  // and 0.409 -> 0.381 ms); at d = 128 the staging cost more than it saved.
+  constexpr bool kRows = MODE == MODE_FEATURES && L <= 6;
+  constexpr int kBuf = kRows && kRowsBuf > WS::VPW * Y::SLOT ? kRowsBuf : WS::VPW * Y::SLOT;
+  __shared__ __align__(16) float sm[kWarps][kBuf];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane / Y::T, lam = lane % Y::T;
   float* buf = sm[warp];
@@ -278,7 +325,10 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_FEATURES ? kWarpMinB
       float acc[CMAX];
 #pragma unroll
       for (int c = 0; c < CMAX; ++c) acc[c] = 0.f;
-      epilogue_A<L, MODE>(P, n, e, valid, lam, w, cs, acc);
+      if constexpr (kRows)
+        epilogue_rows<L>(P, n - g, e, g, lam, w, cs, buf);
+      else
+        epilogue_A<L, MODE>(P, n, e, valid, lam, w, cs, acc);
       if constexpr (MODE == MODE_LOGITS) {
 #pragma unroll
         for (int c = 0; c < CMAX; ++c) {
