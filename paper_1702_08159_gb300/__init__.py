@@ -24,7 +24,7 @@ from . import _lib
 from ._lib import MckError, check, load
 
 __all__ = [
-    "Plan", "MckError", "fwht_", "features", "features_backward", "fused_logits",
+    "Plan", "MckError", "fwht_", "features", "features_host", "features_backward", "fused_logits",
     "fused_logits_backward", "softmax_xent", "library_path",
 ]
 
@@ -183,6 +183,55 @@ def features(plan, x, Cs=None, G=None, out=None):
             raise ValueError("out must be a contiguous (n, 2 E d) tensor")
     check(load().mck_features(plan.handle, _ptr(x), n, in_dim, ld, _ptr(Cs), _ptr(G), _ptr(out),
                               _stream(x.device)), "mck_features")
+    return out
+
+
+def features_host(plan, x, out=None, Cs=None, G=None, chunk_rows=4096, streams=4):
+    """phi(x) for a batch in host memory: x (n, in_dim) float32 on the host
+    (pinned, for copies that overlap), out (n, 2 E d) float32 on the host
+    (pinned; allocated pinned when None). The batch moves in chunks of
+    `chunk_rows` rows over `streams` CUDA streams: each chunk's host-to-device
+    copy, feature kernel and device-to-host copy are queued on one stream, so
+    the copies of different chunks overlap one another and the kernels.
+
+    Stream-ordered like a non_blocking copy: the current stream waits for
+    every chunk, so `out` is complete once the current stream has reached
+    this point (synchronise before reading it on the host)."""
+    if x.is_cuda or x.dtype != torch.float32 or x.dim() != 2:
+        raise TypeError("x must be a 2-d float32 host tensor")
+    x = x.contiguous()
+    n, in_dim = x.shape
+    F = plan.num_features
+    if out is None:
+        out = torch.empty((n, F), dtype=torch.float32, pin_memory=True)
+    elif out.is_cuda or out.dtype != torch.float32 or tuple(out.shape) != (n, F) \
+            or not out.is_contiguous():
+        raise ValueError("out must be a contiguous (n, 2 E d) float32 host tensor")
+    if n == 0:
+        return out
+    dev = torch.device("cuda", plan.device)
+    main = torch.cuda.current_stream(dev)
+    rows = max(1, min(int(chunk_rows), n))
+    k = max(1, min(int(streams), (n + rows - 1) // rows))
+    side = [torch.cuda.Stream(device=dev) for _ in range(k)]
+    bufs = []
+    for s in side:
+        s.wait_stream(main)  # inputs and tables queued before this call
+        xb = torch.empty((rows, in_dim), device=dev, dtype=torch.float32)
+        pb = torch.empty((rows, F), device=dev, dtype=torch.float32)
+        xb.record_stream(s)
+        pb.record_stream(s)
+        bufs.append((xb, pb))
+    for i, a in enumerate(range(0, n, rows)):
+        b = min(a + rows, n)
+        s = side[i % k]
+        xb, pb = bufs[i % k]
+        with torch.cuda.stream(s):
+            xb[: b - a].copy_(x[a:b], non_blocking=True)
+            features(plan, xb[: b - a], Cs, G, out=pb[: b - a])
+            out[a:b].copy_(pb[: b - a], non_blocking=True)
+    for s in side:
+        main.wait_stream(s)
     return out
 
 

@@ -157,6 +157,23 @@ def test_laplace(mck, dev, d, E, n):
     plan.close()
 
 
+@pytest.mark.parametrize("n,chunk,streams", [(1000, 128, 3), (37, 64, 4), (300, 300, 2)])
+def test_features_host_pipeline(mck, dev, n, chunk, streams):
+    """Host-buffer path: chunks over several streams, copies overlapping the
+    kernels; the result equals the device call's bit for bit."""
+    plan = mck.Plan(1024, 3, "rbf", 3.0, 5)
+    x = torch.from_numpy(wl.mnist_like(n, 784, seed=n)).pin_memory()
+    got = mck.features_host(plan, x, chunk_rows=chunk, streams=streams)
+    torch.cuda.synchronize()
+    ref = mck.features(plan, x.to(dev)).cpu()
+    assert torch.equal(got, ref)
+    out = torch.full((n, plan.num_features), float("nan")).pin_memory()
+    mck.features_host(plan, x, out=out, chunk_rows=chunk, streams=streams)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    plan.close()
+
+
 def test_deterministic(mck, dev):
     plan = mck.Plan(1024, 4, "rbf", 1.0, 42)
     x = torch.from_numpy(wl.mnist_like(100, 784, seed=1)).to(dev)
