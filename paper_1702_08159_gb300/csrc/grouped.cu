@@ -12,10 +12,13 @@
 //     2^(L-5) threads in the chunked block form (one 1024-float chunk per
 //     warp); 512/2^(L-5) items of the same d form a unit, each sub-block
 //     synchronising on its own named barrier.
-// Units are ordered by estimated cost, largest first. The persistent kernel
-// runs one 512-thread block per SM; a block takes the next unit with one
-// atomicAdd on a counter (no thread ever waits for another block) until the
-// list is exhausted. mck_group_features allocates nothing and never blocks
+// Units are ordered by estimated cost, largest first, and each is stored as
+// one fixed-size record (block items with their table and vector addresses
+// resolved). The persistent kernel runs one 512-thread block per SM; a block
+// takes units with atomicAdd on a counter (no thread ever waits for another
+// block) until the list is exhausted, two ahead: while a unit runs, the
+// index of the one after next is requested and the next unit's record is
+// copied into shared memory (cp.async). mck_group_features allocates nothing and never blocks
 // the host, so it can be captured in a CUDA graph.
 #include <cuda_runtime.h>
 
@@ -73,13 +76,35 @@ struct GUnit {
   int32_t count;
   int32_t pad;
 };
+// A block item with its addresses resolved at create time: the expansion's
+// lane-ordered tables and the vector's input and output offsets.
+struct alignas(16) GItemRec {
+  const uint32_t* permB;  // + e d
+  const float* GB;        // + e d
+  const uint32_t* maskA;  // + e d / 32
+  const float* Cs;        // + e d
+  int64_t x_off;
+  int64_t phi_off;  // of the expansion's [cos | sin] block
+  int32_t in_dim;
+  int32_t pad[3];
+};
+static_assert(sizeof(GItemRec) == 64, "item record");
+constexpr int kMaxUnitItems = kGThreads >> 6;  // sub-blocks at L = 11
+// Everything a unit needs in one fixed-size record, so the kernel fetches the
+// next unit's with one asynchronous copy instead of a chain of dependent loads.
+struct alignas(16) GUnitRec {
+  GUnit hdr;
+  int32_t pad[2];
+  GItemRec items[kMaxUnitItems];  // block units
+};
+static_assert(sizeof(GUnitRec) % 16 == 0, "unit record");
+constexpr int kUnitRecChunks = (int)(sizeof(GUnitRec) / 16);
 struct GArgs {
   const GPlan* plans;
   const GVec* vecs;
   const GStep* steps;
   const int32_t* step_vecs;
-  const GItem* items;
-  const GUnit* units;
+  const GUnitRec* units;
   int64_t num_units;
   int* counter;
   const float* x;
@@ -193,32 +218,47 @@ __device__ void warp_step(const GArgs& a, const GStep& st, float* buf, int lane)
 // sub-block of 2^(L-5) threads (2^(L-10) warps, one 1024-float chunk each)
 // that synchronises on its own named barrier `bar`.
 template <int L>
-__device__ void block_item(const GArgs& a, const GItem& it, float* buf, int tid, int bar) {
-  constexpr int d = 1 << L;
-  const GPlan pl = a.plans[it.plan];
-  const GVec v = a.vecs[it.vec];
-  const int64_t eo = (int64_t)it.e * d;
-  chunked_map<L>(a.x + v.x_off, v.in_dim, a.vec_x, pl.permB + eo, pl.GB + eo, nullptr,
-                 pl.maskA + eo / 32, pl.Cs + eo, a.phi + v.phi_off + 2 * eo, buf, tid,
-                 [bar] { named_barrier(bar, Chunked<L>::NT); });
+__device__ void block_item(const GArgs& a, const GItemRec& r, float* buf, int tid, int bar) {
+  chunked_map<L>(a.x + r.x_off, r.in_dim, a.vec_x, r.permB, r.GB, nullptr, r.maskA, r.Cs,
+                 a.phi + r.phi_off, buf, tid, [bar] { named_barrier(bar, Chunked<L>::NT); });
 }
 
 __global__ void __launch_bounds__(kGThreads, 1) k_grouped(const GArgs a) {
   extern __shared__ float4 sm4[];
   float* smem = reinterpret_cast<float*>(sm4);
-  __shared__ int s_unit[2];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) s_unit[0] = atomicAdd(a.counter, 1);
+  // Unit indices two ahead (ring of 3: the current unit, the next, and the one
+  // requested while the current runs) and the unit records of the current and
+  // the next unit (double buffer).
+  __shared__ int s_unit[3];
+  __shared__ GUnitRec s_rec[2];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // One commit group per call and thread: unit u's record into slot `slot`.
+  auto fetch_rec = [&](int64_t u, int slot) {
+    if (u < a.num_units && tid < kUnitRecChunks)
+      cp_async16(smem_addr(reinterpret_cast<char*>(&s_rec[slot]) + 16 * tid),
+                 reinterpret_cast<const char*>(a.units + u) + 16 * tid, 16);
+    cp_async_commit();
+  };
+  if (tid == 0) {
+    s_unit[0] = atomicAdd(a.counter, 1);
+    s_unit[1] = atomicAdd(a.counter, 1);
+  }
   __syncthreads();
-  // The next unit's index is requested while the current unit runs (thread 0
-  // holds the pending result in a register and publishes it at the end), so
-  // the atomic's round trip is hidden behind the work.
-  for (int cur = 0;; cur ^= 1) {
+  fetch_rec(s_unit[0], 0);
+  cp_async_wait<0>();
+  __syncthreads();
+  // The index of the unit after next is requested while the current unit runs
+  // (thread 0 holds the pending result in a register and publishes it at the
+  // end), and the next unit's record is copied in meanwhile, so neither the
+  // atomic's round trip nor the record's load is waited for.
+  for (int k = 0;; ++k) {
+    const int cur = k % 3, rb = k & 1;
     const int64_t u = s_unit[cur];
     if (u >= a.num_units) break;
+    fetch_rec(s_unit[(k + 1) % 3], rb ^ 1);
     int next = 0;
-    if (threadIdx.x == 0) next = atomicAdd(a.counter, 1);
-    const GUnit unit = a.units[u];
+    if (tid == 0) next = atomicAdd(a.counter, 1);
+    const GUnit unit = s_rec[rb].hdr;
     if (unit.type == 0) {
       float* buf = smem + warp * kWarpBuf;
       for (int s = warp; s < unit.count; s += kGWarps) {
@@ -235,21 +275,22 @@ __global__ void __launch_bounds__(kGThreads, 1) k_grouped(const GArgs a) {
       }
     } else {
       const int T = 1 << (unit.L - 5);
-      const int sb = threadIdx.x / T, lam = threadIdx.x % T;
+      const int sb = tid / T, lam = tid % T;
       if (sb < unit.count) {
-        const GItem it = a.items[unit.begin + sb];
+        const GItemRec& r = s_rec[rb].items[sb];
         const int slot = (1 << unit.L) + (1 << unit.L) / 32;
         float* buf = smem + sb * slot;
         switch (unit.L) {
-          case 11: block_item<11>(a, it, buf, lam, 1 + sb); break;
-          case 12: block_item<12>(a, it, buf, lam, 1 + sb); break;
-          case 13: block_item<13>(a, it, buf, lam, 1 + sb); break;
-          case 14: block_item<14>(a, it, buf, lam, 1 + sb); break;
+          case 11: block_item<11>(a, r, buf, lam, 1 + sb); break;
+          case 12: block_item<12>(a, r, buf, lam, 1 + sb); break;
+          case 13: block_item<13>(a, r, buf, lam, 1 + sb); break;
+          case 14: block_item<14>(a, r, buf, lam, 1 + sb); break;
           default: break;
         }
       }
     }
-    if (threadIdx.x == 0) s_unit[cur ^ 1] = next;
+    cp_async_wait<0>();  // the next unit's record has landed
+    if (tid == 0) s_unit[(k + 2) % 3] = next;
     __syncthreads();
   }
 }
@@ -273,13 +314,13 @@ struct mck_group_s {
   std::vector<int32_t> step_vecs;
   std::vector<GItem> items;
   std::vector<GUnit> units;
+  std::vector<GUnitRec> unit_recs;
   // device copies
   GPlan* d_plans = nullptr;
   GVec* d_vecs = nullptr;
   GStep* d_steps = nullptr;
   int32_t* d_step_vecs = nullptr;
-  GItem* d_items = nullptr;
-  GUnit* d_units = nullptr;
+  GUnitRec* d_units = nullptr;
   int* d_counter = nullptr;
 };
 
@@ -298,7 +339,6 @@ void free_group_device(mck_group_s* g) {
   cudaFree(g->d_vecs);
   cudaFree(g->d_steps);
   cudaFree(g->d_step_vecs);
-  cudaFree(g->d_items);
   cudaFree(g->d_units);
   cudaFree(g->d_counter);
   cudaGetLastError();
@@ -339,6 +379,22 @@ void build_units(mck_group_s* g) {
   std::stable_sort(list.begin(), list.end(), [](const U& x, const U& y) { return x.cost > y.cost; });
   g->units.clear();
   for (const U& x : list) g->units.push_back(x.u);
+  // one self-contained record per unit: block items with their addresses
+  g->unit_recs.assign(g->units.size(), GUnitRec{});
+  for (size_t k = 0; k < g->units.size(); ++k) {
+    GUnitRec& r = g->unit_recs[k];
+    r.hdr = g->units[k];
+    if (r.hdr.type != 1) continue;
+    const int64_t d = (int64_t)1 << r.hdr.L;
+    for (int i = 0; i < r.hdr.count; ++i) {
+      const GItem& it = g->items[r.hdr.begin + i];
+      const GPlan& pl = g->plans[it.plan];
+      const GVec& v = g->vecs[it.vec];
+      const int64_t eo = (int64_t)it.e * d;
+      r.items[i] = GItemRec{pl.permB + eo, pl.GB + eo, pl.maskA + eo / 32, pl.Cs + eo,
+                            v.x_off, v.phi_off + 2 * eo, v.in_dim, {0, 0, 0}};
+    }
+  }
 }
 
 mck_status_t upload_all(mck_group_s* g) {
@@ -347,15 +403,13 @@ mck_status_t upload_all(mck_group_s* g) {
   g->d_vecs = nullptr;
   g->d_steps = nullptr;
   g->d_step_vecs = nullptr;
-  g->d_items = nullptr;
   g->d_units = nullptr;
   g->d_counter = nullptr;
   cudaError_t err = upload(&g->d_plans, g->plans);
   if (err == cudaSuccess) err = upload(&g->d_vecs, g->vecs);
   if (err == cudaSuccess) err = upload(&g->d_steps, g->steps);
   if (err == cudaSuccess) err = upload(&g->d_step_vecs, g->step_vecs);
-  if (err == cudaSuccess) err = upload(&g->d_items, g->items);
-  if (err == cudaSuccess) err = upload(&g->d_units, g->units);
+  if (err == cudaSuccess) err = upload(&g->d_units, g->unit_recs);
   if (err == cudaSuccess) err = cudaMalloc(&g->d_counter, sizeof(int));
   if (err != cudaSuccess) {
     cudaGetLastError();
@@ -474,7 +528,7 @@ mck_status_t mck_group_set_grain(mck_group_t g, int32_t grain) {
   cudaFree(g->d_steps);
   g->d_steps = nullptr;
   cudaError_t err = upload(&g->d_steps, g->steps);
-  if (err == cudaSuccess) err = upload(&g->d_units, g->units);
+  if (err == cudaSuccess) err = upload(&g->d_units, g->unit_recs);
   if (prev >= 0) cudaSetDevice(prev);
   return err == cudaSuccess ? MCK_OK : cuda_fail(err, "mck_group_set_grain");
 }
@@ -516,7 +570,6 @@ mck_status_t mck_group_features(mck_group_t g, const float* x, float* phi, mck_s
   a.vecs = g->d_vecs;
   a.steps = g->d_steps;
   a.step_vecs = g->d_step_vecs;
-  a.items = g->d_items;
   a.units = g->d_units;
   a.num_units = (int64_t)g->units.size();
   a.counter = g->d_counter;
