@@ -428,12 +428,13 @@ def e2e_leg(mck, plan, x_host, dev, stream, world):
     xin = torch.from_numpy(x_host).pin_memory()
     out_host = torch.empty((N, F), dtype=torch.float32, pin_memory=True)
     phi = None
+    pipe = mck.HostPipeline(plan, IN_DIM, E2E_CHUNK_ROWS, E2E_STREAMS)
 
     def step():
-        mck.features_host(plan, xin, out=out_host, chunk_rows=E2E_CHUNK_ROWS,
-                          streams=E2E_STREAMS)
+        mck.features_host(plan, xin, out=out_host, pipeline=pipe)
 
-    step()
+    for _ in range(2):
+        step()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
@@ -442,7 +443,7 @@ def e2e_leg(mck, plan, x_host, dev, stream, world):
     b.record(stream)
     torch.cuda.synchronize()
     ms = mdist.max_over_ranks(a.elapsed_time(b), device=dev)
-    del out_host, phi
+    del out_host, phi, pipe
     return {"value": world * N * F * steps / (ms / 1e3), "unit": "features/s",
             "h2d_bytes_per_step": N * IN_DIM * 4, "d2h_bytes_per_step": N * F * 4,
             "steps": steps, "ms_per_step": ms / steps,

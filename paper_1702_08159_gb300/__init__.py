@@ -24,7 +24,8 @@ from . import _lib
 from ._lib import MckError, check, load
 
 __all__ = [
-    "Plan", "MckError", "fwht_", "features", "features_host", "features_backward", "fused_logits",
+    "Plan", "MckError", "fwht_", "features", "features_host", "HostPipeline", "features_backward",
+    "fused_logits",
     "fused_logits_backward", "softmax_xent", "library_path",
 ]
 
@@ -186,13 +187,54 @@ def features(plan, x, Cs=None, G=None, out=None):
     return out
 
 
-def features_host(plan, x, out=None, Cs=None, G=None, chunk_rows=4096, streams=4):
+class HostPipeline:
+    """Streams and device buffers for ``features_host``, made once and reused:
+    `streams` CUDA streams, each with a chunk of `chunk_rows` input rows
+    (in_dim wide) and of their features on the plan's device. Each stream
+    only ever reuses its own buffers, after its previous chunk, so calls need
+    no allocation and no extra synchronisation."""
+
+    def __init__(self, plan, in_dim, chunk_rows=2048, streams=4):
+        dev = torch.device("cuda", plan.device)
+        self.plan, self.in_dim = plan, int(in_dim)
+        self.rows = max(1, int(chunk_rows))
+        self.streams = [torch.cuda.Stream(device=dev) for _ in range(max(1, int(streams)))]
+        self.bufs = [(torch.empty((self.rows, self.in_dim), device=dev, dtype=torch.float32),
+                      torch.empty((self.rows, plan.num_features), device=dev, dtype=torch.float32))
+                     for _ in self.streams]
+
+    def run(self, x, out, Cs=None, G=None):
+        """Features of the host batch x into the host array out; stream-ordered
+        (the current stream waits for every chunk)."""
+        plan = self.plan
+        n = x.shape[0]
+        main = torch.cuda.current_stream(torch.device("cuda", plan.device))
+        k = min(len(self.streams), (n + self.rows - 1) // self.rows)
+        for s in self.streams[:k]:
+            s.wait_stream(main)  # inputs, tables and the previous call's readers
+        for i, a in enumerate(range(0, n, self.rows)):
+            b = min(a + self.rows, n)
+            s = self.streams[i % k]
+            xb, pb = self.bufs[i % k]
+            with torch.cuda.stream(s):
+                xb[: b - a].copy_(x[a:b], non_blocking=True)
+                features(plan, xb[: b - a], Cs, G, out=pb[: b - a])
+                out[a:b].copy_(pb[: b - a], non_blocking=True)
+        for s in self.streams[:k]:
+            main.wait_stream(s)
+        return out
+
+
+def features_host(plan, x, out=None, Cs=None, G=None, chunk_rows=2048, streams=4,
+                  pipeline=None):
     """phi(x) for a batch in host memory: x (n, in_dim) float32 on the host
     (pinned, for copies that overlap), out (n, 2 E d) float32 on the host
     (pinned; allocated pinned when None). The batch moves in chunks of
     `chunk_rows` rows over `streams` CUDA streams: each chunk's host-to-device
     copy, feature kernel and device-to-host copy are queued on one stream, so
-    the copies of different chunks overlap one another and the kernels.
+    the copies of different chunks overlap one another and the kernels. A
+    ``HostPipeline`` made once (same plan and in_dim) avoids allocating the
+    streams and device buffers on every call.
 
     Stream-ordered like a non_blocking copy: the current stream waits for
     every chunk, so `out` is complete once the current stream has reached
@@ -209,30 +251,11 @@ def features_host(plan, x, out=None, Cs=None, G=None, chunk_rows=4096, streams=4
         raise ValueError("out must be a contiguous (n, 2 E d) float32 host tensor")
     if n == 0:
         return out
-    dev = torch.device("cuda", plan.device)
-    main = torch.cuda.current_stream(dev)
-    rows = max(1, min(int(chunk_rows), n))
-    k = max(1, min(int(streams), (n + rows - 1) // rows))
-    side = [torch.cuda.Stream(device=dev) for _ in range(k)]
-    bufs = []
-    for s in side:
-        s.wait_stream(main)  # inputs and tables queued before this call
-        xb = torch.empty((rows, in_dim), device=dev, dtype=torch.float32)
-        pb = torch.empty((rows, F), device=dev, dtype=torch.float32)
-        xb.record_stream(s)
-        pb.record_stream(s)
-        bufs.append((xb, pb))
-    for i, a in enumerate(range(0, n, rows)):
-        b = min(a + rows, n)
-        s = side[i % k]
-        xb, pb = bufs[i % k]
-        with torch.cuda.stream(s):
-            xb[: b - a].copy_(x[a:b], non_blocking=True)
-            features(plan, xb[: b - a], Cs, G, out=pb[: b - a])
-            out[a:b].copy_(pb[: b - a], non_blocking=True)
-    for s in side:
-        main.wait_stream(s)
-    return out
+    if pipeline is None:
+        pipeline = HostPipeline(plan, in_dim, min(int(chunk_rows), n), streams)
+    elif pipeline.plan is not plan or pipeline.in_dim != in_dim:
+        raise ValueError("pipeline was made for another plan or input width")
+    return pipeline.run(x, out, Cs, G)
 
 
 def features_backward(plan, x, dphi, Cs=None, G=None, need_dx=True, need_dCs=True, need_dG=True,

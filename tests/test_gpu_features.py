@@ -171,6 +171,14 @@ def test_features_host_pipeline(mck, dev, n, chunk, streams):
     mck.features_host(plan, x, out=out, chunk_rows=chunk, streams=streams)
     torch.cuda.synchronize()
     assert torch.equal(out, ref)
+    # a pipeline made once and reused for two batches back to back
+    pipe = mck.HostPipeline(plan, 784, chunk, streams)
+    x2 = torch.from_numpy(wl.mnist_like(n, 784, seed=n + 1)).pin_memory()
+    o1 = mck.features_host(plan, x, pipeline=pipe)
+    o2 = mck.features_host(plan, x2, pipeline=pipe)
+    torch.cuda.synchronize()
+    assert torch.equal(o1, ref)
+    assert torch.equal(o2, mck.features(plan, x2.to(dev)).cpu())
     plan.close()
 
 
