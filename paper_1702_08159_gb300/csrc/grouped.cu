@@ -56,10 +56,15 @@ struct GVec {
   int32_t in_dim;
   int32_t E;
 };
+// A warp step with its expansion's lane-ordered tables resolved at create time
+// (pointers already offset to expansion e); its vectors' descriptors sit in
+// step_vdesc[vdesc_begin ...] with phi_off already pointing at expansion e.
 struct GStep {
-  int64_t vec_begin;  // into step_vecs
-  int32_t plan;
-  int32_t e;
+  int64_t vdesc_begin;
+  const uint32_t* permB;
+  const float* GB;
+  const uint32_t* maskA;
+  const float* Cs;
   int32_t L;
   int32_t count;
 };
@@ -100,10 +105,8 @@ struct alignas(16) GUnitRec {
 static_assert(sizeof(GUnitRec) % 16 == 0, "unit record");
 constexpr int kUnitRecChunks = (int)(sizeof(GUnitRec) / 16);
 struct GArgs {
-  const GPlan* plans;
-  const GVec* vecs;
   const GStep* steps;
-  const int32_t* step_vecs;
+  const GVec* step_vdesc;
   const GUnitRec* units;
   int64_t num_units;
   int* counter;
@@ -159,20 +162,19 @@ __device__ __forceinline__ void store_features_A(float* __restrict__ out, int la
   }
 }
 
-// One warp step (5 <= L <= 10): group g of the warp handles vector g of the step.
+// One warp step (5 <= L <= 10): group g of the warp handles vector g of the
+// step; the tables are the step's resolved pointers (one dependent load less
+// than going through the plan), the vector descriptors a flat array.
 template <int L>
-__device__ void warp_step(const GArgs& a, const GStep& st, float* buf, int lane) {
+__device__ __forceinline__ void warp_step(const GArgs& a, const GStep& st, float* buf, int lane) {
   using Y = Lay<L>;
-  constexpr int d = Y::d;
   const int g = lane / Y::T, lam = lane % Y::T;
-  const GPlan pl = a.plans[st.plan];
-  const int64_t off = (int64_t)st.e * d;
-  const uint32_t bmask = __ldg(pl.maskA + (int64_t)st.e * Y::T + lam);
   const uint32_t slot = smem_addr(buf) + 4u * (uint32_t)(g * Y::SLOT);
+  const uint32_t bmask = __ldg(st.maskA + lam);
   uint32_t poff[16];
   float gt[32];
-  const uint4* pb = reinterpret_cast<const uint4*>(pl.permB + off) + lam;
-  const float4* gb = reinterpret_cast<const float4*>(pl.GB + off) + lam;
+  const uint4* pb = reinterpret_cast<const uint4*>(st.permB) + lam;
+  const float4* gb = reinterpret_cast<const float4*>(st.GB) + lam;
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const uint4 v = __ldg(pb + m * Y::T);
@@ -186,7 +188,7 @@ __device__ void warp_step(const GArgs& a, const GStep& st, float* buf, int lane)
   }
   const bool valid = g < st.count;
   GVec v{};
-  if (valid) v = a.vecs[a.step_vecs[st.vec_begin + g]];
+  if (valid) v = a.step_vdesc[st.vdesc_begin + g];
   float w[32];
   load_row_A<L>(a.x + v.x_off, v.in_dim, a.vec_x, valid, lam, w);
   apply_signs(w, bmask);
@@ -210,8 +212,21 @@ __device__ void warp_step(const GArgs& a, const GStep& st, float* buf, int lane)
     load_A<L>(buf, g, lam, w);
   }
   hreg<Y::maskA()>(w);
-  if (valid) store_features_A<L>(a.phi + v.phi_off + 2 * off, lam, w, pl.Cs + off);
+  if (valid) store_features_A<L>(a.phi + v.phi_off, lam, w, st.Cs);
   __syncwarp();
+}
+
+// A warp's steps of one unit (all of one L): steps warp, warp + 16, ...
+// (the next step's record is requested into L1 while this one runs)
+template <int L>
+__device__ __forceinline__ void warp_steps(const GArgs& a, const GUnit& unit, float* buf, int warp,
+                                           int lane) {
+  for (int s = warp; s < unit.count; s += kGWarps) {
+    const GStep st = a.steps[unit.begin + s];
+    if (s + kGWarps < unit.count && lane == 0)
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(a.steps + unit.begin + s + kGWarps));
+    warp_step<L>(a, st, buf, lane);
+  }
 }
 
 // One block item (11 <= L <= 14): the chunked block form of the map on a
@@ -261,17 +276,14 @@ __global__ void __launch_bounds__(kGThreads, 1) k_grouped(const GArgs a) {
     const GUnit unit = s_rec[rb].hdr;
     if (unit.type == 0) {
       float* buf = smem + warp * kWarpBuf;
-      for (int s = warp; s < unit.count; s += kGWarps) {
-        const GStep st = a.steps[unit.begin + s];
-        switch (st.L) {
-          case 5: warp_step<5>(a, st, buf, lane); break;
-          case 6: warp_step<6>(a, st, buf, lane); break;
-          case 7: warp_step<7>(a, st, buf, lane); break;
-          case 8: warp_step<8>(a, st, buf, lane); break;
-          case 9: warp_step<9>(a, st, buf, lane); break;
-          case 10: warp_step<10>(a, st, buf, lane); break;
-          default: break;
-        }
+      switch (unit.L) {
+        case 5: warp_steps<5>(a, unit, buf, warp, lane); break;
+        case 6: warp_steps<6>(a, unit, buf, warp, lane); break;
+        case 7: warp_steps<7>(a, unit, buf, warp, lane); break;
+        case 8: warp_steps<8>(a, unit, buf, warp, lane); break;
+        case 9: warp_steps<9>(a, unit, buf, warp, lane); break;
+        case 10: warp_steps<10>(a, unit, buf, warp, lane); break;
+        default: break;
       }
     } else {
       const int T = 1 << (unit.L - 5);
@@ -311,15 +323,13 @@ struct mck_group_s {
   std::vector<GPlan> plans;
   std::vector<GVec> vecs;
   std::vector<GStep> steps;
-  std::vector<int32_t> step_vecs;
+  std::vector<GVec> step_vdesc;
   std::vector<GItem> items;
   std::vector<GUnit> units;
   std::vector<GUnitRec> unit_recs;
   // device copies
-  GPlan* d_plans = nullptr;
-  GVec* d_vecs = nullptr;
   GStep* d_steps = nullptr;
-  int32_t* d_step_vecs = nullptr;
+  GVec* d_step_vdesc = nullptr;
   GUnitRec* d_units = nullptr;
   int* d_counter = nullptr;
 };
@@ -335,10 +345,8 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
 }
 
 void free_group_device(mck_group_s* g) {
-  cudaFree(g->d_plans);
-  cudaFree(g->d_vecs);
   cudaFree(g->d_steps);
-  cudaFree(g->d_step_vecs);
+  cudaFree(g->d_step_vdesc);
   cudaFree(g->d_units);
   cudaFree(g->d_counter);
   cudaGetLastError();
@@ -359,12 +367,19 @@ void build_units(mck_group_s* g) {
   std::vector<GStep> sorted(g->steps.size());
   for (size_t i = 0; i < order.size(); ++i) sorted[i] = g->steps[order[i]];
   g->steps.swap(sorted);
+  // a unit holds steps of one L only (the kernel keeps that L's tables in
+  // registers across the unit's steps)
   const int per_unit = kGWarps * std::max(1, g->grain);
-  for (int64_t b = 0; b < (int64_t)g->steps.size(); b += per_unit) {
-    const int cnt = (int)std::min<int64_t>(per_unit, (int64_t)g->steps.size() - b);
+  for (int64_t b = 0; b < (int64_t)g->steps.size();) {
+    const int L = g->steps[b].L;
+    int cnt = 0;
     double cost = 0.0;
-    for (int i = 0; i < cnt; ++i) cost += unit_cost(g->steps[b + i].L, g->steps[b + i].count);
-    list.push_back({GUnit{b, 0, 0, cnt, 0}, cost / kGWarps});
+    while (cnt < per_unit && b + cnt < (int64_t)g->steps.size() && g->steps[b + cnt].L == L) {
+      cost += unit_cost(L, g->steps[b + cnt].count);
+      ++cnt;
+    }
+    list.push_back({GUnit{b, 0, L, cnt, 0}, cost / kGWarps});
+    b += cnt;
   }
   // block items: all items of one L are contiguous (sorted at create time)
   int64_t b = 0;
@@ -399,16 +414,12 @@ void build_units(mck_group_s* g) {
 
 mck_status_t upload_all(mck_group_s* g) {
   free_group_device(g);
-  g->d_plans = nullptr;
-  g->d_vecs = nullptr;
   g->d_steps = nullptr;
-  g->d_step_vecs = nullptr;
+  g->d_step_vdesc = nullptr;
   g->d_units = nullptr;
   g->d_counter = nullptr;
-  cudaError_t err = upload(&g->d_plans, g->plans);
-  if (err == cudaSuccess) err = upload(&g->d_vecs, g->vecs);
-  if (err == cudaSuccess) err = upload(&g->d_steps, g->steps);
-  if (err == cudaSuccess) err = upload(&g->d_step_vecs, g->step_vecs);
+  cudaError_t err = upload(&g->d_steps, g->steps);
+  if (err == cudaSuccess) err = upload(&g->d_step_vdesc, g->step_vdesc);
   if (err == cudaSuccess) err = upload(&g->d_units, g->unit_recs);
   if (err == cudaSuccess) err = cudaMalloc(&g->d_counter, sizeof(int));
   if (err != cudaSuccess) {
@@ -483,8 +494,15 @@ mck_status_t mck_group_create(mck_group_t* out, const mck_plan_t* plans, int32_t
         while (cnt < (int64_t)vs.size() && g->vecs[vs[cnt]].E > e) ++cnt;
         for (int64_t b = 0; b < cnt; b += vpw) {
           const int c = (int)std::min<int64_t>(vpw, cnt - b);
-          g->steps.push_back(GStep{(int64_t)g->step_vecs.size(), p, e, L, c});
-          for (int k = 0; k < c; ++k) g->step_vecs.push_back(vs[b + k]);
+          const GPlan& pl = g->plans[p];
+          const int64_t eo = (int64_t)e << L;
+          g->steps.push_back(GStep{(int64_t)g->step_vdesc.size(), pl.permB + eo, pl.GB + eo,
+                                   pl.maskA + ((int64_t)e << (L - 5)), pl.Cs + eo, L, c});
+          for (int k = 0; k < c; ++k) {
+            GVec v = g->vecs[vs[b + k]];
+            v.phi_off += 2 * eo;  // expansion e's [cos | sin] block
+            g->step_vdesc.push_back(v);
+          }
         }
       }
     } else {
@@ -566,10 +584,8 @@ mck_status_t mck_group_features(mck_group_t g, const float* x, float* phi, mck_s
   cudaGetDevice(&prev);
   if (prev != g->device) cudaSetDevice(g->device);
   GArgs a{};
-  a.plans = g->d_plans;
-  a.vecs = g->d_vecs;
   a.steps = g->d_steps;
-  a.step_vecs = g->d_step_vecs;
+  a.step_vdesc = g->d_step_vdesc;
   a.units = g->d_units;
   a.num_units = (int64_t)g->units.size();
   a.counter = g->d_counter;
