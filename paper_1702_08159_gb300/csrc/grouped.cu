@@ -162,12 +162,18 @@ __device__ __forceinline__ void store_features_A(float* __restrict__ out, int la
   }
 }
 
-// One warp step (5 <= L <= 10): group g of the warp handles vector g of the
-// step; the tables are the step's resolved pointers (one dependent load less
-// than going through the plan), the vector descriptors a flat array.
+// Vectors per warp step: VPW = 32 / 2^(L-5) at a time, R times over (the
+// tables are loaded once per step: R = 4 at d = 1024, 2 at 512, 1 below).
+__host__ __device__ constexpr int step_rounds(int L) { return L >= 10 ? 4 : (L == 9 ? 2 : 1); }
+
+// One warp step (5 <= L <= 10): group g of the warp handles vectors g,
+// g + VPW, ... of the step; the tables are the step's resolved pointers (one
+// dependent load less than going through the plan), the vector descriptors a
+// flat array.
 template <int L>
 __device__ __forceinline__ void warp_step(const GArgs& a, const GStep& st, float* buf, int lane) {
   using Y = Lay<L>;
+  constexpr int VPW = 32 / Y::T;
   const int g = lane / Y::T, lam = lane % Y::T;
   const uint32_t slot = smem_addr(buf) + 4u * (uint32_t)(g * Y::SLOT);
   const uint32_t bmask = __ldg(st.maskA + lam);
@@ -186,9 +192,13 @@ __device__ __forceinline__ void warp_step(const GArgs& a, const GStep& st, float
     gt[4 * m + 2] = q.z;
     gt[4 * m + 3] = q.w;
   }
-  const bool valid = g < st.count;
+#pragma unroll 1
+  for (int r = 0; r < step_rounds(L); ++r) {
+  const int k = r * VPW + g;
+  if (r * VPW >= st.count) break;
+  const bool valid = k < st.count;
   GVec v{};
-  if (valid) v = a.step_vdesc[st.vdesc_begin + g];
+  if (valid) v = a.step_vdesc[st.vdesc_begin + k];
   float w[32];
   load_row_A<L>(a.x + v.x_off, v.in_dim, a.vec_x, valid, lam, w);
   apply_signs(w, bmask);
@@ -214,6 +224,7 @@ __device__ __forceinline__ void warp_step(const GArgs& a, const GStep& st, float
   hreg<Y::maskA()>(w);
   if (valid) store_features_A<L>(a.phi + v.phi_off, lam, w, st.Cs);
   __syncwarp();
+  }
 }
 
 // A warp's steps of one unit (all of one L): steps warp, warp + 16, ...
@@ -487,7 +498,7 @@ mck_status_t mck_group_create(mck_group_t* out, const mck_plan_t* plans, int32_t
     std::stable_sort(vs.begin(), vs.end(),
                      [&](int32_t a, int32_t b) { return g->vecs[a].E > g->vecs[b].E; });
     if (L <= 10) {
-      const int vpw = 32 >> (L - 5);
+      const int vpw = (32 >> (L - 5)) * step_rounds(L);  // vectors per step
       const int emax = vs.empty() ? 0 : g->vecs[vs[0]].E;
       for (int e = 0; e < emax; ++e) {
         int64_t cnt = 0;  // vectors using expansion e: a prefix of vs
