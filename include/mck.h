@@ -251,25 +251,28 @@ typedef struct {
  * synchronous). plans: host array of num_plans plans on one device with
  * 32 <= d <= 2^14. items: host array. x_len / phi_len: the element counts of
  * the x and phi arrays later passed to mck_group_features; every item must
- * fit inside them. grain: warp steps per warp in one unit of work (0 picks
- * the default, 2); a tunable, see mck_group_set_grain. Feature layout of an
- * item: E blocks of [cos (d) | sin (d)] at phi + phi_offset. */
+ * fit inside them. grain: warp steps a warp takes from the work counter at a
+ * time (0 picks the default, 2); a tunable, see mck_group_set_grain. Feature
+ * layout of an item: E blocks of [cos (d) | sin (d)] at phi + phi_offset. */
 mck_status_t mck_group_create(mck_group_t* out, const mck_plan_t* plans, int32_t num_plans,
                               const mck_group_item_t* items, int64_t num_items, int64_t x_len,
                               int64_t phi_len, int32_t grain);
 
-/* Rebuild the unit list with another grain (1..64); synchronises the device. */
+/* Set the grain (1..64) used by later launches (a CUDA graph captured
+ * earlier keeps the grain it was captured with). Host only. */
 mck_status_t mck_group_set_grain(mck_group_t group, int32_t grain);
 
-/* Sizes of the work list; any output may be NULL. */
+/* Sizes of the work list; any output may be NULL. num_units: the number of
+ * phases (one per kind of work and d: block items of one d, or warp steps of
+ * one d), each run to completion by all blocks before the next. */
 mck_status_t mck_group_info(mck_group_t group, int64_t* num_units, int64_t* num_warp_steps,
                             int64_t* num_block_items, int32_t* grain);
 
-/* Features of every item of the group: one memset of the work counter and
+/* Features of every item of the group: one memset of the work counters and
  * one persistent kernel launch on `stream`. Allocates nothing and does not
  * synchronise, so the call can be captured in a CUDA graph. x (x_len floats)
  * and phi (phi_len floats, 16-byte aligned) are device arrays. Calls on one
- * group must not overlap on the GPU (they share the work counter). */
+ * group must not overlap on the GPU (they share the work counters). */
 mck_status_t mck_group_features(mck_group_t group, const float* x, float* phi,
                                 mck_stream_t stream);
 

@@ -4,22 +4,24 @@
 // Z-hat, so a vector may use any prefix of a plan's expansions).
 //
 // mck_group_create turns the items into a work list once:
-//   * d <= 1024: "warp steps" -- up to 32/2^(L-5) vectors that share a plan
-//     and an expansion, processed by one warp exactly like the batched
-//     feature kernel (register layouts A and B, lane-ordered tables);
-//     16 * grain steps form a unit.
+//   * d <= 1024: "warp steps" -- up to 32/2^(L-5) vectors (4x as many at
+//     d = 1024, 2x at 512, in rounds that share one table load) that share a
+//     plan and an expansion, processed by one warp like the batched feature
+//     kernel (register layouts A and B, lane-ordered tables);
 //   * d >= 2048: "block items" -- one (vector, expansion) for a sub-block of
 //     2^(L-5) threads in the chunked block form (one 1024-float chunk per
-//     warp); 512/2^(L-5) items of the same d form a unit, each sub-block
-//     synchronising on its own named barrier.
-// Units are ordered by estimated cost, largest first, and each is stored as
-// one fixed-size record (block items with their table and vector addresses
-// resolved). The persistent kernel runs one 512-thread block per SM; a block
-// takes units with atomicAdd on a counter (no thread ever waits for another
-// block) until the list is exhausted, two ahead: while a unit runs, the
-// index of the one after next is requested and the next unit's record is
-// copied into shared memory (cp.async). mck_group_features allocates nothing and never blocks
-// the host, so it can be captured in a CUDA graph.
+//     warp), each sub-block synchronising on its own named barrier.
+// The work runs in phases, one per kind and size, largest items first: all
+// block items of d = 2^14, then 2^13, ..., then the warp steps of d = 1024
+// down to 32. Within a phase every sub-block (or warp) takes its next item
+// (or `grain` steps) from the phase's own atomic counter, independently of
+// the others, requesting the one after while the current runs and copying
+// its record (addresses resolved at create time) into shared memory with
+// cp.async; the block synchronises only between phases, where the shared
+// memory is partitioned anew. The persistent kernel runs one 512-thread
+// block per SM; no thread ever waits for another block. mck_group_features
+// allocates nothing and never blocks the host, so it can be captured in a
+// CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,9 +37,8 @@ namespace mck {
 namespace {
 
 constexpr int kGThreads = 512;
-constexpr int kGWarps = kGThreads / 32;
 constexpr int kWarpBuf = 1152;      // floats: the largest VPW * SLOT (L = 5)
-constexpr int kSmemFloats = 18432;  // max(16 * kWarpBuf, 512/T sub-blocks * SLOT)
+constexpr int kSmemFloats = 18432;  // max(16 warps x kWarpBuf, 512/T sub-blocks x SLOT)
 
 struct GPlan {
   const uint32_t* permB;
@@ -74,13 +75,6 @@ struct GItem {
   int32_t e;
   int32_t L;
 };
-struct GUnit {
-  int64_t begin;
-  int32_t type;  // 0: warp steps, 1: block items
-  int32_t L;     // block items: their common L
-  int32_t count;
-  int32_t pad;
-};
 // A block item with its addresses resolved at create time: the expansion's
 // lane-ordered tables and the vector's input and output offsets.
 struct alignas(16) GItemRec {
@@ -94,25 +88,32 @@ struct alignas(16) GItemRec {
   int32_t pad[3];
 };
 static_assert(sizeof(GItemRec) == 64, "item record");
-constexpr int kMaxUnitItems = kGThreads >> 6;  // sub-blocks at L = 11
-// Everything a unit needs in one fixed-size record, so the kernel fetches the
-// next unit's with one asynchronous copy instead of a chain of dependent loads.
-struct alignas(16) GUnitRec {
-  GUnit hdr;
-  int32_t pad[2];
-  GItemRec items[kMaxUnitItems];  // block units
+// A phase: the block items (type 1) or the warp steps (type 0) of one L.
+struct GPhase {
+  int64_t begin;  // into items (type 1) or steps (type 0)
+  int64_t count;
+  int32_t type;
+  int32_t L;
 };
-static_assert(sizeof(GUnitRec) % 16 == 0, "unit record");
-constexpr int kUnitRecChunks = (int)(sizeof(GUnitRec) / 16);
 struct GArgs {
   const GStep* steps;
   const GVec* step_vdesc;
-  const GUnitRec* units;
-  int64_t num_units;
-  int* counter;
+  const GItemRec* items;
+  const GPhase* phases;
+  int32_t num_phases;
+  int32_t grain;  // warp steps per fetch
+  int* counters;  // one per phase, zero at launch
   const float* x;
   float* phi;
   bool vec_x;
+};
+constexpr int kMaxSubs = kGThreads >> 6;  // sub-blocks at L = 11
+// Per sub-block state of a block phase, in shared memory: item indices two
+// ahead (ring of 3) and the records of the current and the next item.
+struct alignas(16) SubState {
+  int idx[3];
+  int pad;
+  GItemRec rec[2];
 };
 
 __device__ __forceinline__ void apply_signs(float (&w)[32], uint32_t mask) {
@@ -227,98 +228,108 @@ __device__ __forceinline__ void warp_step(const GArgs& a, const GStep& st, float
   }
 }
 
-// A warp's steps of one unit (all of one L): steps warp, warp + 16, ...
-// (the next step's record is requested into L1 while this one runs)
-template <int L>
-__device__ __forceinline__ void warp_steps(const GArgs& a, const GUnit& unit, float* buf, int warp,
-                                           int lane) {
-  for (int s = warp; s < unit.count; s += kGWarps) {
-    const GStep st = a.steps[unit.begin + s];
-    if (s + kGWarps < unit.count && lane == 0)
-      asm volatile("prefetch.global.L1 [%0];" ::"l"(a.steps + unit.begin + s + kGWarps));
-    warp_step<L>(a, st, buf, lane);
-  }
-}
-
 // One block item (11 <= L <= 14): the chunked block form of the map on a
 // sub-block of 2^(L-5) threads (2^(L-10) warps, one 1024-float chunk each)
 // that synchronises on its own named barrier `bar`.
 template <int L>
-__device__ void block_item(const GArgs& a, const GItemRec& r, float* buf, int tid, int bar) {
+__device__ __forceinline__ void block_item(const GArgs& a, const GItemRec& r, float* buf, int tid,
+                                           int bar) {
   chunked_map<L>(a.x + r.x_off, r.in_dim, a.vec_x, r.permB, r.GB, nullptr, r.maskA, r.Cs,
                  a.phi + r.phi_off, buf, tid, [bar] { named_barrier(bar, Chunked<L>::NT); });
+}
+
+// A block phase: each sub-block takes items from the phase's counter until
+// none are left. The index after next is requested while an item runs (the
+// sub-block's first thread holds the pending result and publishes it at the
+// end) and the next item's record is copied into shared memory meanwhile.
+template <int L>
+__device__ void block_phase(const GArgs& a, const GPhase& ph, int* ctr, float* smem,
+                            SubState* subs, int tid) {
+  constexpr int NT = Chunked<L>::NT;  // threads per sub-block
+  const int sb = tid / NT, lam = tid % NT, bar = 1 + sb;
+  SubState& S = subs[sb];
+  float* buf = smem + sb * ((1 << L) + (1 << L) / 32);
+  // one commit group per call and thread: item i's record into slot `slot`
+  auto fetch = [&](int64_t i, int slot) {
+    if (i < ph.count && lam < 4)
+      cp_async16(smem_addr(reinterpret_cast<char*>(&S.rec[slot]) + 16 * lam),
+                 reinterpret_cast<const char*>(a.items + ph.begin + i) + 16 * lam, 16);
+    cp_async_commit();
+  };
+  if (lam == 0) {
+    S.idx[0] = atomicAdd(ctr, 1);
+    S.idx[1] = atomicAdd(ctr, 1);
+  }
+  named_barrier(bar, NT);
+  fetch(S.idx[0], 0);
+  cp_async_wait<0>();
+  named_barrier(bar, NT);
+  for (int k = 0;; ++k) {
+    const int64_t i = S.idx[k % 3];
+    if (i >= ph.count) break;
+    fetch(S.idx[(k + 1) % 3], (k & 1) ^ 1);
+    int next = 0;
+    if (lam == 0) next = atomicAdd(ctr, 1);
+    block_item<L>(a, S.rec[k & 1], buf, lam, bar);
+    cp_async_wait<0>();  // the next item's record has landed
+    if (lam == 0) S.idx[(k + 2) % 3] = next;
+    named_barrier(bar, NT);
+  }
+}
+
+// A warp phase: each warp takes `grain` steps at a time from the phase's
+// counter (the next batch requested while the current one runs).
+template <int L>
+__device__ void warp_phase(const GArgs& a, const GPhase& ph, int* ctr, float* buf, int lane) {
+  const int grain = a.grain;
+  int s0 = 0;
+  if (lane == 0) s0 = atomicAdd(ctr, grain);
+  s0 = __shfl_sync(0xffffffffu, s0, 0);
+  while (s0 < ph.count) {
+    int s1 = 0;
+    if (lane == 0) s1 = atomicAdd(ctr, grain);
+    const int64_t end = std::min<int64_t>((int64_t)s0 + grain, ph.count);
+    for (int64_t s = s0; s < end; ++s) {
+      const GStep st = a.steps[ph.begin + s];
+      if (s + 1 < end && lane == 0)
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(a.steps + ph.begin + s + 1));
+      warp_step<L>(a, st, buf, lane);
+    }
+    s0 = __shfl_sync(0xffffffffu, s1, 0);
+  }
 }
 
 __global__ void __launch_bounds__(kGThreads, 1) k_grouped(const GArgs a) {
   extern __shared__ float4 sm4[];
   float* smem = reinterpret_cast<float*>(sm4);
-  // Unit indices two ahead (ring of 3: the current unit, the next, and the one
-  // requested while the current runs) and the unit records of the current and
-  // the next unit (double buffer).
-  __shared__ int s_unit[3];
-  __shared__ GUnitRec s_rec[2];
+  __shared__ SubState s_sub[kMaxSubs];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // One commit group per call and thread: unit u's record into slot `slot`.
-  auto fetch_rec = [&](int64_t u, int slot) {
-    if (u < a.num_units && tid < kUnitRecChunks)
-      cp_async16(smem_addr(reinterpret_cast<char*>(&s_rec[slot]) + 16 * tid),
-                 reinterpret_cast<const char*>(a.units + u) + 16 * tid, 16);
-    cp_async_commit();
-  };
-  if (tid == 0) {
-    s_unit[0] = atomicAdd(a.counter, 1);
-    s_unit[1] = atomicAdd(a.counter, 1);
-  }
-  __syncthreads();
-  fetch_rec(s_unit[0], 0);
-  cp_async_wait<0>();
-  __syncthreads();
-  // The index of the unit after next is requested while the current unit runs
-  // (thread 0 holds the pending result in a register and publishes it at the
-  // end), and the next unit's record is copied in meanwhile, so neither the
-  // atomic's round trip nor the record's load is waited for.
-  for (int k = 0;; ++k) {
-    const int cur = k % 3, rb = k & 1;
-    const int64_t u = s_unit[cur];
-    if (u >= a.num_units) break;
-    fetch_rec(s_unit[(k + 1) % 3], rb ^ 1);
-    int next = 0;
-    if (tid == 0) next = atomicAdd(a.counter, 1);
-    const GUnit unit = s_rec[rb].hdr;
-    if (unit.type == 0) {
-      float* buf = smem + warp * kWarpBuf;
-      switch (unit.L) {
-        case 5: warp_steps<5>(a, unit, buf, warp, lane); break;
-        case 6: warp_steps<6>(a, unit, buf, warp, lane); break;
-        case 7: warp_steps<7>(a, unit, buf, warp, lane); break;
-        case 8: warp_steps<8>(a, unit, buf, warp, lane); break;
-        case 9: warp_steps<9>(a, unit, buf, warp, lane); break;
-        case 10: warp_steps<10>(a, unit, buf, warp, lane); break;
+  for (int p = 0; p < a.num_phases; ++p) {
+    const GPhase ph = a.phases[p];
+    int* ctr = a.counters + p;
+    if (ph.type == 1) {
+      switch (ph.L) {
+        case 11: block_phase<11>(a, ph, ctr, smem, s_sub, tid); break;
+        case 12: block_phase<12>(a, ph, ctr, smem, s_sub, tid); break;
+        case 13: block_phase<13>(a, ph, ctr, smem, s_sub, tid); break;
+        case 14: block_phase<14>(a, ph, ctr, smem, s_sub, tid); break;
         default: break;
       }
     } else {
-      const int T = 1 << (unit.L - 5);
-      const int sb = tid / T, lam = tid % T;
-      if (sb < unit.count) {
-        const GItemRec& r = s_rec[rb].items[sb];
-        const int slot = (1 << unit.L) + (1 << unit.L) / 32;
-        float* buf = smem + sb * slot;
-        switch (unit.L) {
-          case 11: block_item<11>(a, r, buf, lam, 1 + sb); break;
-          case 12: block_item<12>(a, r, buf, lam, 1 + sb); break;
-          case 13: block_item<13>(a, r, buf, lam, 1 + sb); break;
-          case 14: block_item<14>(a, r, buf, lam, 1 + sb); break;
-          default: break;
-        }
+      float* buf = smem + warp * kWarpBuf;
+      switch (ph.L) {
+        case 5: warp_phase<5>(a, ph, ctr, buf, lane); break;
+        case 6: warp_phase<6>(a, ph, ctr, buf, lane); break;
+        case 7: warp_phase<7>(a, ph, ctr, buf, lane); break;
+        case 8: warp_phase<8>(a, ph, ctr, buf, lane); break;
+        case 9: warp_phase<9>(a, ph, ctr, buf, lane); break;
+        case 10: warp_phase<10>(a, ph, ctr, buf, lane); break;
+        default: break;
       }
     }
-    cp_async_wait<0>();  // the next unit's record has landed
-    if (tid == 0) s_unit[(k + 2) % 3] = next;
-    __syncthreads();
+    __syncthreads();  // the next phase partitions shared memory anew
   }
 }
-
-double unit_cost(int L, int64_t vectors) { return (double)vectors * (double)(L + 4) * (1 << L); }
 
 }  // namespace
 }  // namespace mck
@@ -336,13 +347,14 @@ struct mck_group_s {
   std::vector<GStep> steps;
   std::vector<GVec> step_vdesc;
   std::vector<GItem> items;
-  std::vector<GUnit> units;
-  std::vector<GUnitRec> unit_recs;
+  std::vector<GItemRec> item_recs;
+  std::vector<GPhase> phases;
   // device copies
   GStep* d_steps = nullptr;
   GVec* d_step_vdesc = nullptr;
-  GUnitRec* d_units = nullptr;
-  int* d_counter = nullptr;
+  GItemRec* d_items = nullptr;
+  GPhase* d_phases = nullptr;
+  int* d_counters = nullptr;
 };
 
 namespace {
@@ -358,68 +370,39 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
 void free_group_device(mck_group_s* g) {
   cudaFree(g->d_steps);
   cudaFree(g->d_step_vdesc);
-  cudaFree(g->d_units);
-  cudaFree(g->d_counter);
+  cudaFree(g->d_items);
+  cudaFree(g->d_phases);
+  cudaFree(g->d_counters);
   cudaGetLastError();
 }
 
-// Units for the current grain, ordered by cost (largest first).
-void build_units(mck_group_s* g) {
-  struct U {
-    GUnit u;
-    double cost;
-  };
-  std::vector<U> list;
-  // warp steps, grouped by L so a unit's warps do similar work
-  std::vector<int64_t> order(g->steps.size());
-  for (size_t i = 0; i < order.size(); ++i) order[i] = (int64_t)i;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int64_t a, int64_t b) { return g->steps[a].L > g->steps[b].L; });
-  std::vector<GStep> sorted(g->steps.size());
-  for (size_t i = 0; i < order.size(); ++i) sorted[i] = g->steps[order[i]];
-  g->steps.swap(sorted);
-  // a unit holds steps of one L only (the kernel keeps that L's tables in
-  // registers across the unit's steps)
-  const int per_unit = kGWarps * std::max(1, g->grain);
+// The phases: block items by L (largest first), then warp steps by L (largest
+// first); steps and items are sorted so that each phase is one contiguous run.
+void build_phases(mck_group_s* g) {
+  std::stable_sort(g->steps.begin(), g->steps.end(),
+                   [](const GStep& a, const GStep& b) { return a.L > b.L; });
+  std::stable_sort(g->items.begin(), g->items.end(),
+                   [](const GItem& a, const GItem& b) { return a.L > b.L; });
+  g->item_recs.clear();
+  for (const GItem& it : g->items) {
+    const GPlan& pl = g->plans[it.plan];
+    const GVec& v = g->vecs[it.vec];
+    const int64_t eo = (int64_t)it.e << it.L;
+    g->item_recs.push_back(GItemRec{pl.permB + eo, pl.GB + eo, pl.maskA + eo / 32, pl.Cs + eo,
+                                    v.x_off, v.phi_off + 2 * eo, v.in_dim, {0, 0, 0}});
+  }
+  g->phases.clear();
+  for (int64_t b = 0; b < (int64_t)g->items.size();) {
+    int64_t e = b;
+    while (e < (int64_t)g->items.size() && g->items[e].L == g->items[b].L) ++e;
+    g->phases.push_back(GPhase{b, e - b, 1, g->items[b].L});
+    b = e;
+  }
   for (int64_t b = 0; b < (int64_t)g->steps.size();) {
-    const int L = g->steps[b].L;
-    int cnt = 0;
-    double cost = 0.0;
-    while (cnt < per_unit && b + cnt < (int64_t)g->steps.size() && g->steps[b + cnt].L == L) {
-      cost += unit_cost(L, g->steps[b + cnt].count);
-      ++cnt;
-    }
-    list.push_back({GUnit{b, 0, L, cnt, 0}, cost / kGWarps});
-    b += cnt;
-  }
-  // block items: all items of one L are contiguous (sorted at create time)
-  int64_t b = 0;
-  while (b < (int64_t)g->items.size()) {
-    const int L = g->items[b].L;
-    const int per = kGThreads >> (L - 5);
-    int cnt = 0;
-    while (cnt < per && b + cnt < (int64_t)g->items.size() && g->items[b + cnt].L == L) ++cnt;
-    list.push_back({GUnit{b, 1, L, cnt, 0}, unit_cost(L, 1)});
-    b += cnt;
-  }
-  std::stable_sort(list.begin(), list.end(), [](const U& x, const U& y) { return x.cost > y.cost; });
-  g->units.clear();
-  for (const U& x : list) g->units.push_back(x.u);
-  // one self-contained record per unit: block items with their addresses
-  g->unit_recs.assign(g->units.size(), GUnitRec{});
-  for (size_t k = 0; k < g->units.size(); ++k) {
-    GUnitRec& r = g->unit_recs[k];
-    r.hdr = g->units[k];
-    if (r.hdr.type != 1) continue;
-    const int64_t d = (int64_t)1 << r.hdr.L;
-    for (int i = 0; i < r.hdr.count; ++i) {
-      const GItem& it = g->items[r.hdr.begin + i];
-      const GPlan& pl = g->plans[it.plan];
-      const GVec& v = g->vecs[it.vec];
-      const int64_t eo = (int64_t)it.e * d;
-      r.items[i] = GItemRec{pl.permB + eo, pl.GB + eo, pl.maskA + eo / 32, pl.Cs + eo,
-                            v.x_off, v.phi_off + 2 * eo, v.in_dim, {0, 0, 0}};
-    }
+    int64_t e = b;
+    while (e < (int64_t)g->steps.size() && g->steps[e].L == g->steps[b].L) ++e;
+    g->phases.push_back(GPhase{b, e - b, 0, g->steps[b].L});
+    b = e;
   }
 }
 
@@ -427,12 +410,15 @@ mck_status_t upload_all(mck_group_s* g) {
   free_group_device(g);
   g->d_steps = nullptr;
   g->d_step_vdesc = nullptr;
-  g->d_units = nullptr;
-  g->d_counter = nullptr;
+  g->d_items = nullptr;
+  g->d_phases = nullptr;
+  g->d_counters = nullptr;
   cudaError_t err = upload(&g->d_steps, g->steps);
   if (err == cudaSuccess) err = upload(&g->d_step_vdesc, g->step_vdesc);
-  if (err == cudaSuccess) err = upload(&g->d_units, g->unit_recs);
-  if (err == cudaSuccess) err = cudaMalloc(&g->d_counter, sizeof(int));
+  if (err == cudaSuccess) err = upload(&g->d_items, g->item_recs);
+  if (err == cudaSuccess) err = upload(&g->d_phases, g->phases);
+  if (err == cudaSuccess && !g->phases.empty())
+    err = cudaMalloc(&g->d_counters, sizeof(int) * g->phases.size());
   if (err != cudaSuccess) {
     cudaGetLastError();
     return fail(MCK_ENOMEM, "group work list upload failed");
@@ -521,9 +507,7 @@ mck_status_t mck_group_create(mck_group_t* out, const mck_plan_t* plans, int32_t
         for (int e = 0; e < g->vecs[v].E; ++e) g->items.push_back(GItem{v, p, e, L});
     }
   }
-  std::stable_sort(g->items.begin(), g->items.end(),
-                   [](const GItem& a, const GItem& b) { return a.L > b.L; });
-  build_units(g);
+  build_phases(g);
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(device);
@@ -546,26 +530,14 @@ mck_status_t mck_group_create(mck_group_t* out, const mck_plan_t* plans, int32_t
 mck_status_t mck_group_set_grain(mck_group_t g, int32_t grain) {
   if (!g) return fail(MCK_EINVAL, "group is NULL");
   if (grain < 1 || grain > 64) return fail(MCK_EINVAL, "grain must be in [1, 64]");
-  int prev = -1;
-  cudaGetDevice(&prev);
-  cudaSetDevice(g->device);
-  cudaDeviceSynchronize();  // no queued launch may still read the old unit list
-  g->grain = grain;
-  build_units(g);
-  cudaFree(g->d_units);
-  g->d_units = nullptr;
-  cudaFree(g->d_steps);
-  g->d_steps = nullptr;
-  cudaError_t err = upload(&g->d_steps, g->steps);
-  if (err == cudaSuccess) err = upload(&g->d_units, g->unit_recs);
-  if (prev >= 0) cudaSetDevice(prev);
-  return err == cudaSuccess ? MCK_OK : cuda_fail(err, "mck_group_set_grain");
+  g->grain = grain;  // read at the next launch (a captured graph keeps its own)
+  return MCK_OK;
 }
 
 mck_status_t mck_group_info(mck_group_t g, int64_t* num_units, int64_t* num_steps,
                             int64_t* num_block_items, int32_t* grain) {
   if (!g) return fail(MCK_EINVAL, "group is NULL");
-  if (num_units) *num_units = (int64_t)g->units.size();
+  if (num_units) *num_units = (int64_t)g->phases.size();
   if (num_steps) *num_steps = (int64_t)g->steps.size();
   if (num_block_items) *num_block_items = (int64_t)g->items.size();
   if (grain) *grain = g->grain;
@@ -585,7 +557,7 @@ void mck_group_destroy(mck_group_t g) {
 
 mck_status_t mck_group_features(mck_group_t g, const float* x, float* phi, mck_stream_t stream) {
   if (!g) return fail(MCK_EINVAL, "group is NULL");
-  if (g->units.empty()) return MCK_OK;
+  if (g->phases.empty()) return MCK_OK;
   if (!x || !phi) return fail(MCK_EINVAL, "x and phi must not be NULL");
   if ((uintptr_t)phi % 16) return fail(MCK_EINVAL, "phi must be 16-byte aligned");
   mck_status_t st = check_device_array(x, 4 * g->x_len, g->device, "x");
@@ -597,16 +569,21 @@ mck_status_t mck_group_features(mck_group_t g, const float* x, float* phi, mck_s
   GArgs a{};
   a.steps = g->d_steps;
   a.step_vdesc = g->d_step_vdesc;
-  a.units = g->d_units;
-  a.num_units = (int64_t)g->units.size();
-  a.counter = g->d_counter;
+  a.items = g->d_items;
+  a.phases = g->d_phases;
+  a.num_phases = (int32_t)g->phases.size();
+  a.grain = g->grain;
+  a.counters = g->d_counters;
   a.x = x;
   a.phi = phi;
   a.vec_x = g->vec_x && ((uintptr_t)x % 16 == 0);
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t err = cudaMemsetAsync(g->d_counter, 0, sizeof(int), s);
+  cudaError_t err = cudaMemsetAsync(g->d_counters, 0, sizeof(int) * g->phases.size(), s);
   if (err == cudaSuccess) {
-    const unsigned grid = (unsigned)std::max(1, std::min<int>(g->num_sms, (int)g->units.size()));
+    // every block takes part in every phase (it leaves a phase when the
+    // phase's counter runs past its work)
+    const int64_t work = (int64_t)g->items.size() + (int64_t)g->steps.size();
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(g->num_sms, work));
     k_grouped<<<grid, kGThreads, sizeof(float) * kSmemFloats, s>>>(a);
     err = cudaGetLastError();
   }
