@@ -1,8 +1,9 @@
 """Autotuner for grouped (uneven-batch) launches.
 
-The tunable is the grain of mck_group_create: how many warp steps one warp
-takes from each unit of work. Small grains balance load better; large grains
-cost fewer atomic fetches and keep a block's warps on similar work. The tuner
+The tunable is the grain of mck_group_create: how many warp steps a warp
+takes from its phase's work counter at a time. Small grains balance the end
+of each phase better; large grains cost fewer atomic fetches on the one
+counter every warp of the GPU draws from. The tuner
 times each candidate on the caller's own data with CUDA events and keeps the
 fastest; results are cached in a JSON file keyed by the batch's signature
 (the multiset of (d, E, kernel) per item and the GPU name), so the sweep runs
