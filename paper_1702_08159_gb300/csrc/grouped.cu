@@ -40,16 +40,13 @@ constexpr int kGThreads = 512;
 constexpr int kWarpBuf = 1152;      // floats: the largest VPW * SLOT (L = 5)
 constexpr int kSmemFloats = 18432;  // max(16 warps x kWarpBuf, 512/T sub-blocks x SLOT)
 
+// A plan's lane-ordered tables (host side, for resolving steps and items).
 struct GPlan {
   const uint32_t* permB;
   const float* GB;
   const uint32_t* maskA;
   const float* Cs;
-  const uint32_t* bits;
-  const uint32_t* perm;
-  const float* G;
   int32_t L;
-  int32_t Emax;
 };
 struct GVec {
   int64_t x_off;
@@ -453,7 +450,7 @@ mck_status_t mck_group_create(mck_group_t* out, const mck_plan_t* plans, int32_t
   g->grain = grain ? grain : 2;
   for (int32_t p = 0; p < num_plans; ++p) {
     const mck_plan_s* q = plans[p];
-    g->plans.push_back(GPlan{q->permB, q->GB, q->maskA, q->Cs, q->B_bits, q->perm, q->G, q->L, q->E});
+    g->plans.push_back(GPlan{q->permB, q->GB, q->maskA, q->Cs, q->L});
   }
   // per-plan vector lists (for warp steps) and validation
   std::vector<std::vector<int32_t>> by_plan(num_plans);
