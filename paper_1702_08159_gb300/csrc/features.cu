@@ -200,7 +200,7 @@ struct WarpShape {
   static constexpr int SPI = VPW * R;                // samples per item
 };
 
-template <int L, int MODE>
+template <int L, int MODE, bool ONE = false>
 __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_FEATURES ? kWarpMinBlocks : 12) k_feat_warp(const Launch P) {
   using Y = Lay<L>;
   using WS = WarpShape<L>;
@@ -216,7 +216,11 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_FEATURES ? kWarpMinB
   const uint32_t buf_addr = smem_addr(buf);
 
   const int E = P.a.E;
-  const int64_t tiles = (P.a.n + WS::SPI - 1) / WS::SPI;
+  // Tiles of R rounds of VPW samples; ONE (a small batch: fewer full tiles
+  // than resident warps) runs one round per tile, so that more warps share it.
+  constexpr int R = ONE ? 1 : WS::R;
+  constexpr int spi = WS::VPW * R;
+  const int64_t tiles = (P.a.n + spi - 1) / spi;
   const int64_t items = tiles * E;
   const int64_t nw = (int64_t)gridDim.x * kWarps;
   const int64_t wid = (int64_t)blockIdx.x * kWarps + warp;
@@ -278,8 +282,8 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_FEATURES ? kWarpMinB
         cs[4 * m + 3] = v.w;
       }
     }
-    for (int r = 0; r < WS::R; ++r) {
-      const int64_t n = tile * WS::SPI + r * WS::VPW + g;
+    for (int r = 0; r < R; ++r) {
+      const int64_t n = tile * spi + r * WS::VPW + g;
       const bool valid = n < P.a.n;
       float w[32];
       load_x_A<L>(P, n, valid, lam, w);
@@ -287,13 +291,13 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_FEATURES ? kWarpMinB
       {
         int64_t nn;
         bool more = true;
-        if (r + 1 < WS::R) {
+        if (r + 1 < R) {
           nn = n + WS::VPW;
         } else {
           const int64_t it2 = it + 1;
           more = it2 < it1;
           const int64_t tile2 = (MODE == MODE_FEATURES) ? it2 / E : it2 % tiles;
-          nn = tile2 * WS::SPI + g;
+          nn = tile2 * spi + g;
         }
         if (more && nn < P.a.n && (int64_t)lam * 32 < P.a.in_dim)
           asm volatile("prefetch.global.L1 [%0];" ::"l"(P.a.x + nn * P.a.ldx + lam * 32));
@@ -885,10 +889,21 @@ cudaError_t run(const Launch& P, cudaStream_t s) {
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms * occ));
     k_feat_tiny<L, MODE><<<grid, 128, 0, s>>>(P);
   } else if constexpr (L <= 10) {
+    using WS = WarpShape<L>;
     const int occ = occ_blocks(k_feat_warp<L, MODE>, kWarps * 32, 0);
-    const int64_t items = (P.a.n + WarpShape<L>::SPI - 1) / WarpShape<L>::SPI * P.a.E;
-    const int64_t need = (items + kWarps - 1) / kWarps;
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms * occ));
+    const int64_t slots = (int64_t)num_sms * occ * kWarps;  // resident warps
+    const int64_t full = (P.a.n + WS::SPI - 1) / WS::SPI * P.a.E;
+    if constexpr (WS::R > 1) {
+      if (full < slots) {  // a small batch: one round of VPW samples per item
+        const int64_t items = (P.a.n + WS::VPW - 1) / WS::VPW * P.a.E;
+        const unsigned grid = (unsigned)std::max<int64_t>(
+            1, std::min<int64_t>((items + kWarps - 1) / kWarps, slots / kWarps));
+        k_feat_warp<L, MODE, true><<<grid, kWarps * 32, 0, s>>>(P);
+        return cudaGetLastError();
+      }
+    }
+    const int64_t need = (full + kWarps - 1) / kWarps;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, slots / kWarps));
     k_feat_warp<L, MODE><<<grid, kWarps * 32, 0, s>>>(P);
   } else if constexpr (MODE == MODE_FEATURES && L <= 14) {
     // Staging pays at 2^14 only, where one block per SM leaves nothing to
