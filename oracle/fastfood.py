@@ -24,7 +24,7 @@ layout (c0, c1, c2, c3) = (index, expansion e, tag, sub-draw) and key = the
   5 Matern ball coordinates (c2 = 5 + 16*k), 6 Matern ball radius,
   7 the normal divisor of the Laplacian radius.
 
-Readings of points the paper leaves open (each also listed in the design doc):
+Readings of points the paper leaves open:
   * B[k] = -1 when bit 0 of word 0 is set, else +1.
   * Fisher-Yates draws j = floor(w0 * (i+1) / 2**32) for i = d-1 .. 1 and swaps
     L[i], L[j]; (Pi v)_k = v_{pi(k)} (a gather).
