@@ -93,7 +93,7 @@ typedef enum {
 mck_status_t mck_plan(mck_plan_t* out, int64_t d, int32_t E, int32_t kernel, double sigma,
                       uint64_t seed);
 
-/* As mck_plan, with the Matern order t (1 <= t <= 4096; ignored for RBF) and
+/* As mck_plan, with the Matern order t (1 <= t <= 4096; ignored for RBF and Laplace) and
  * the CUDA device index (-1 = current device). */
 mck_status_t mck_plan_ex(mck_plan_t* out, int64_t d, int32_t E, int32_t kernel, double sigma,
                          int32_t matern_t, uint64_t seed, int32_t device);

@@ -102,3 +102,47 @@ def test_binding_refuses_missing_library(tmp_path, monkeypatch):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(RuntimeError, match="no fallback"):
         _lib.load()
+
+
+C_CALLER = r"""
+#include <stdio.h>
+#include <string.h>
+#include "mck.h"
+
+int main(void) {
+  mck_plan_t p = 0;
+  /* argument checks run on the host before any device work */
+  mck_status_t s = mck_plan(&p, 3, 1, MCK_RBF, 1.0, 1u);
+  if (s != MCK_EINVAL || p != 0) return 1;
+  s = mck_plan_ex(&p, 1024, 1, MCK_LAPLACE + 1, 1.0, 40, 1u, -1);
+  if (s != MCK_EINVAL) return 2;
+  if (strncmp(mck_status_string(MCK_EUNSUPPORTED), "MCK_", 4) != 0) return 3;
+  if (mck_last_error() == 0 || mck_last_error()[0] == 0) return 4;
+  mck_plan_destroy(0);
+  printf("ok\n");
+  return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """A C99 program includes mck.h, links libmck.so and gets the host-side
+    argument errors: the boundary needs neither C++ nor Python."""
+    import shutil
+    import subprocess
+
+    from paper_1702_08159_gb300 import _lib
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    src = tmp_path / "caller.c"
+    src.write_text(C_CALLER)
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(_lib.LIB_PATH)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe), "-L", libdir, "-l:libmck.so",
+                        "-Wl,-rpath," + libdir], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0 and run.stdout.strip() == "ok", (run.returncode, run.stderr)
