@@ -91,22 +91,52 @@ __host__ __device__ __forceinline__ constexpr int spos(int g, int k) {
   return g * Lay<L>::SLOT + pad(k);
 }
 
-// H over the register bits in MASK (unnormalised butterflies).
-template <unsigned MASK>
-__device__ __forceinline__ void hreg(float (&w)[32]) {
+// Packed FP32 pairs (two lanes of FP32 arithmetic per instruction). Each
+// half rounds exactly like the scalar operation; a - c is formed as
+// fma(c, -1, a), which is exact before its one rounding.
+__device__ __forceinline__ float2 add2(float2 a, float2 c) { return __fadd2_rn(a, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 c) {
+  return __ffma2_rn(c, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 c) { return __fmul2_rn(a, c); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// One butterfly stage over register bit b >= 1: pairs (j, j+1) with bit 0
+// clear are one packed operand, so two butterflies issue as one add and one
+// subtract.
+template <int b>
+__device__ __forceinline__ void hstage2(float (&w)[32]) {
+  static_assert(b >= 1 && b < 5, "packed stages need bit 0 inside the pair");
 #pragma unroll
-  for (int b = 0; b < 5; ++b) {
-    if (MASK >> b & 1u) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        if (!(j >> b & 1)) {
-          const float a = w[j], c = w[j | (1 << b)];
-          w[j] = a + c;
-          w[j | (1 << b)] = a - c;
-        }
-      }
+  for (int j = 0; j < 32; j += 2) {
+    if (!(j >> b & 1)) {
+      const int jc = j | (1 << b);
+      const float2 a = make_float2(w[j], w[j + 1]), c = make_float2(w[jc], w[jc + 1]);
+      const float2 s = add2(a, c), t = sub2(a, c);
+      w[j] = s.x;
+      w[j + 1] = s.y;
+      w[jc] = t.x;
+      w[jc + 1] = t.y;
     }
   }
+}
+
+// H over the register bits in MASK (unnormalised butterflies), bit 0 first
+// (scalar: its pairs share one packed operand), then bits 1..4 packed.
+template <unsigned MASK>
+__device__ __forceinline__ void hreg(float (&w)[32]) {
+  if constexpr ((MASK & 1u) != 0) {
+#pragma unroll
+    for (int j = 0; j < 32; j += 2) {
+      const float a = w[j], c = w[j + 1];
+      w[j] = a + c;
+      w[j + 1] = a - c;
+    }
+  }
+  if constexpr ((MASK & 2u) != 0) hstage2<1>(w);
+  if constexpr ((MASK & 4u) != 0) hstage2<2>(w);
+  if constexpr ((MASK & 8u) != 0) hstage2<3>(w);
+  if constexpr ((MASK & 16u) != 0) hstage2<4>(w);
 }
 
 template <unsigned MASK>
@@ -120,14 +150,29 @@ template <unsigned MASK>
 __device__ __forceinline__ void hreg_scaled(float (&w)[32], const float (&s)[32]) {
   static_assert(MASK != 0, "scaled transform needs at least one bit");
   constexpr int b0 = lowest_bit<MASK>();
+  if constexpr (b0 == 0) {
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    if (!(j >> b0 & 1)) {
-      const int jc = j | (1 << b0);
+    for (int j = 0; j < 32; j += 2) {
       const float a = s[j] * w[j];
-      const float c = w[jc];
-      w[j] = fmaf(s[jc], c, a);
-      w[jc] = fmaf(-s[jc], c, a);
+      const float c = w[j + 1];
+      w[j] = fmaf(s[j + 1], c, a);
+      w[j + 1] = fmaf(-s[j + 1], c, a);
+    }
+  } else {
+    // packed: a = s_a w_a as one product, then c' = a -/+ s_c w_c as fmas
+#pragma unroll
+    for (int j = 0; j < 32; j += 2) {
+      if (!(j >> b0 & 1)) {
+        const int jc = j | (1 << b0);
+        const float2 a = mul2(make_float2(s[j], s[j + 1]), make_float2(w[j], w[j + 1]));
+        const float2 sc = make_float2(s[jc], s[jc + 1]), c = make_float2(w[jc], w[jc + 1]);
+        const float2 p = fma2(sc, c, a);
+        const float2 m = fma2(make_float2(-sc.x, -sc.y), c, a);
+        w[j] = p.x;
+        w[j + 1] = p.y;
+        w[jc] = m.x;
+        w[jc + 1] = m.y;
+      }
     }
   }
   hreg<MASK & ~(1u << b0)>(w);
@@ -142,6 +187,29 @@ __device__ __forceinline__ void cos_sin(float z, float& c, float& s) {
   r = fmaf(-k, kTwoPiLo, r);
   c = __cosf(r);
   s = __sinf(r);
+}
+
+// cos and sin of z = cs * h for two values at once: the same arithmetic as
+// cos_sin(cs * h) (with -k = rint(-z / 2 pi), exact since rounding to nearest
+// is symmetric), the products and reductions as packed pairs.
+__device__ __forceinline__ void cos_sin2(float2 cs, float2 h, float2& c, float2& s) {
+  const float2 z = mul2(cs, h);
+  const float2 t = mul2(z, make_float2(-kInvTwoPi, -kInvTwoPi));
+  const float2 kn = make_float2(rintf(t.x), rintf(t.y));
+  float2 r = fma2(kn, make_float2(kTwoPiHi, kTwoPiHi), z);
+  r = fma2(kn, make_float2(kTwoPiLo, kTwoPiLo), r);
+  c = make_float2(__cosf(r.x), __cosf(r.y));
+  s = make_float2(__sinf(r.x), __sinf(r.y));
+}
+
+// cos and sin of cs[q] * h[q] for a register quad.
+__device__ __forceinline__ void cos_sin4(const float* cs, const float* h, float (&c)[4],
+                                         float (&s)[4]) {
+  float2 c0, s0, c1, s1;
+  cos_sin2(make_float2(cs[0], cs[1]), make_float2(h[0], h[1]), c0, s0);
+  cos_sin2(make_float2(cs[2], cs[3]), make_float2(h[2], h[3]), c1, s1);
+  c[0] = c0.x; c[1] = c0.y; c[2] = c1.x; c[3] = c1.y;
+  s[0] = s0.x; s[1] = s0.y; s[2] = s1.x; s[3] = s1.y;
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -286,10 +354,12 @@ __device__ __forceinline__ void chunk_columns_inplace(float* sm, int tid) {
       for (int i = 0; i < C::W; ++i)
         if (!(i & h))
 #pragma unroll
-          for (int v = 0; v < C::VEC; ++v) {
-            const float a = u[i][v], b = u[i | h][v];
-            u[i][v] = a + b;
-            u[i | h][v] = a - b;
+          for (int v = 0; v < C::VEC; v += 2) {
+            const float2 a = make_float2(u[i][v], u[i][v + 1]);
+            const float2 b = make_float2(u[i | h][v], u[i | h][v + 1]);
+            const float2 s = add2(a, b), t = sub2(a, b);
+            u[i][v] = s.x; u[i][v + 1] = s.y;
+            u[i | h][v] = t.x; u[i | h][v + 1] = t.y;
           }
 #pragma unroll
     for (int i = 0; i < C::W; ++i) st_vec<C::VEC>(sm + i * C::SLOT + pad(c0), u[i]);
@@ -427,10 +497,12 @@ __device__ __forceinline__ void chunked_map_impl(const float* __restrict__ xrow,
       for (int i = 0; i < C::W; ++i)
         if (!(i & h))
 #pragma unroll
-          for (int v = 0; v < C::VEC; ++v) {
-            const float a = u[i][v], b = u[i | h][v];
-            u[i][v] = a + b;
-            u[i | h][v] = a - b;
+          for (int v = 0; v < C::VEC; v += 2) {
+            const float2 a = make_float2(u[i][v], u[i][v + 1]);
+            const float2 b = make_float2(u[i | h][v], u[i | h][v + 1]);
+            const float2 s = add2(a, b), t = sub2(a, b);
+            u[i][v] = s.x; u[i][v + 1] = s.y;
+            u[i | h][v] = t.x; u[i | h][v + 1] = t.y;
           }
 #pragma unroll
     for (int i = 0; i < C::W; ++i) {
@@ -439,7 +511,12 @@ __device__ __forceinline__ void chunked_map_impl(const float* __restrict__ xrow,
       if constexpr (STAGED) ld_vec<C::VEC>(css + k, cv);
       else ld_vec<C::VEC>(cs + k, cv);
 #pragma unroll
-      for (int v = 0; v < C::VEC; ++v) cos_sin(cv[v] * u[i][v], cz[v], sz[v]);
+      for (int v = 0; v < C::VEC; v += 2) {
+        float2 c2, s2;
+        cos_sin2(make_float2(cv[v], cv[v + 1]), make_float2(u[i][v], u[i][v + 1]), c2, s2);
+        cz[v] = c2.x; cz[v + 1] = c2.y;
+        sz[v] = s2.x; sz[v + 1] = s2.y;
+      }
       if constexpr (C::VEC == 4) {
         __stcs(reinterpret_cast<float4*>(out + k), make_float4(cz[0], cz[1], cz[2], cz[3]));
         __stcs(reinterpret_cast<float4*>(out + d + k), make_float4(sz[0], sz[1], sz[2], sz[3]));

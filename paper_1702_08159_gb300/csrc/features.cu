@@ -111,8 +111,7 @@ __device__ __forceinline__ void epilogue_A(const Launch& P, int64_t n, int e, bo
   for (int m = 0; m < 8; ++m) {
     const int k0 = Lay<L>::kA(lam, 4 * m);
     float c[4], s[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) cos_sin(cs[4 * m + q] * h[4 * m + q], c[q], s[q]);
+    cos_sin4(&cs[4 * m], &h[4 * m], c, s);
     if constexpr (MODE == MODE_FEATURES) {
       if (valid) {
         float* o = P.phi + n * F + 2ll * e * d + k0;
@@ -163,8 +162,7 @@ __device__ __forceinline__ void epilogue_rows(const Launch& P, int64_t n0, int e
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     float c[4], s4[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) cos_sin(cs[4 * m + q] * h[4 * m + q], c[q], s4[q]);
+    cos_sin4(&cs[4 * m], &h[4 * m], c, s4);
     const int at = g * RS + Y::kA(lam, 4 * m);
     *reinterpret_cast<float4*>(buf + at) = make_float4(c[0], c[1], c[2], c[3]);
     *reinterpret_cast<float4*>(buf + HALF + at) = make_float4(s4[0], s4[1], s4[2], s4[3]);
@@ -746,8 +744,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_logits_tile(const Launch P,
           const float4 c4 = __ldg(reinterpret_cast<const float4*>(P.a.Cs + off + k0));
           const float cs[4] = {c4.x, c4.y, c4.z, c4.w};
           float c[4], s4[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) cos_sin(cs[q] * w[4 * m + q], c[q], s4[q]);
+          cos_sin4(cs, &w[4 * m], c, s4);
           // an invalid row contributes nothing
           if (!valid) c[0] = c[1] = c[2] = c[3] = s4[0] = s4[1] = s4[2] = s4[3] = 0.f;
           *reinterpret_cast<float4*>(buf + k0) = make_float4(c[0], c[1], c[2], c[3]);

@@ -153,8 +153,7 @@ __device__ __forceinline__ void store_features_A(float* __restrict__ out, int la
     const float4 c4 = __ldg(reinterpret_cast<const float4*>(Cs + k0));
     const float cs[4] = {c4.x, c4.y, c4.z, c4.w};
     float c[4], s[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) cos_sin(cs[q] * h[4 * m + q], c[q], s[q]);
+    cos_sin4(cs, &h[4 * m], c, s);
     __stcs(reinterpret_cast<float4*>(out + k0), make_float4(c[0], c[1], c[2], c[3]));
     __stcs(reinterpret_cast<float4*>(out + d + k0), make_float4(s[0], s[1], s[2], s[3]));
   }

@@ -1,7 +1,7 @@
 // Training-side kernels: the softmax cross-entropy of Sec. "Empirical
 // Analysis" (the multi-class form of the logistic loss, Eq. etn:loss) and the
 // adjoint of the Fastfood feature map, which Sec. "Empirical Analysis"
-// motivates ("learn the appropriate Calibration C and G" by backpropagation).
+// motivates (the calibration C and the Gaussian G are trained by backpropagation).
 //
 // The adjoint recomputes the forward and runs the chain rule backwards,
 // using H^T = H (Sylvester H is symmetric) and Pi^T = Pi^{-1} (the gather
@@ -338,10 +338,10 @@ __device__ __forceinline__ void bwd_core(const BwdLaunch& P, const BwdTabs& tb, 
       csq[0] = c4.x; csq[1] = c4.y; csq[2] = c4.z; csq[3] = c4.w;
     }
     float cz[4], sz[4], hz[4];
+    cos_sin4(csq, &w[4 * m], cz, sz);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = 4 * m + q;
-      cos_sin(csq[q] * w[j], cz[q], sz[q]);
       const float dz = fmaf(-sz[q], dc[j], cz[q] * ds[j]);
       hz[q] = w[j] * dz;
       w[j] = csq[q] * dz;  // dh
