@@ -7,7 +7,7 @@
  *   phi(x) = [cos(Z-hat x-hat), sin(Z-hat x-hat)] per expansion  (Eq. etn:mcfeatures)
  *
  * with x-hat = x zero-padded to d = 2^L (Fig. 1 caption), E independent
- * expansions (Sec. "McKernel": "generate multiple instances of Z-hat"), and
+ * expansions (Sec. "McKernel": Z-hat is instantiated E times), and
  * the classifier softmax(W phi + b) of Sec. "Empirical Analysis and
  * Experiments". B (signs), Pi (permutation), G (Gaussian) and the calibration
  * C are recreated from a seed by a counter-based hash (Sec. "API
@@ -196,19 +196,25 @@ mck_status_t mck_fused_logits(mck_plan_t plan, const float* x, int64_t n, int64_
  * failure mid-request, or code that manages all device memory through its
  * own pool and forbids other allocations.
  *
- * Instead of stream-ordered scratch, the n x E x num_classes partial logits
- * go to an array of MCK_NOALLOC_MAX_PARTIALS floats (16 MiB) compiled into
- * the library; each GPU on which the library is used holds its own copy
- * until the process exits. Requests with n * E * num_classes above that size
- * return MCK_EINVAL before any work is queued (split the batch instead).
- * The first call on a device looks up the array's device address (with that
- * device current) and caches it; make that first call before any stream
- * capture. The call performs no cudaMalloc or cudaFree and calls no
- * allocating library routine. All calls share the one array per device and
- * every call fully overwrites the part it uses, so nothing carries over from
- * a previous call; but calls whose work overlaps on the GPU (different
- * streams, or different threads) race on the array and must be serialised by
- * the caller. */
+ * Instead of stream-ordered scratch, the partial logits go to an array of
+ * MCK_NOALLOC_MAX_PARTIALS floats (16 MiB) compiled into the library; each
+ * GPU on which the library is used holds its own copy until the process
+ * exits. How many partials a call needs depends on its shape: none at
+ * d = 1024 when the batch has at least 8 rows per SM (the tile kernel writes
+ * the logits directly; the 60000 x E = 16 x 10-class MNIST-shaped batch is
+ * one such call), n x (expansion chunks) x num_classes for smaller batches at
+ * d = 1024, and n x E x num_classes at every other d. A call that would need
+ * more than the array holds returns MCK_EINVAL before any work is queued
+ * (split the batch instead). The first call on a device looks up the
+ * array's device address (with that device current) and caches it; make
+ * that first call before any stream capture. The cached address belongs to
+ * the device's current CUDA context: after cudaDeviceReset (or any teardown
+ * of the primary context) every later call is invalid, as plans are. The
+ * call performs no cudaMalloc or cudaFree and calls no allocating library
+ * routine. All calls share the one array per device and every call fully
+ * overwrites the part it uses, so nothing carries over from a previous call;
+ * but calls whose work overlaps on the GPU (different streams, or different
+ * threads) race on the array and must be serialised by the caller. */
 mck_status_t mck_fused_logits_noalloc(mck_plan_t plan, const float* x, int64_t n, int64_t in_dim,
                                       int64_t ldx, const float* Cs, const float* G,
                                       const float* W, const float* b, int32_t num_classes,

@@ -573,11 +573,15 @@ extern "C" mck_status_t mck_fused_logits_noalloc(mck_plan_t p, const float* x, i
                                                  int32_t C, float* logits, mck_stream_t stream) {
   MCK_TRY(check_plan(p));
   if (C < 1 || C > MCK_MAX_CLASSES) return fail(MCK_EINVAL, "num_classes must be in [1, 16]");
-  if (n > 0 && n * (int64_t)p->E * C > (int64_t)MCK_NOALLOC_MAX_PARTIALS)
-    return fail(MCK_EINVAL, "n * E * num_classes = " + std::to_string(n * (int64_t)p->E * C) +
+  // The kernels pick the amount of partial logits from the batch shape: none
+  // at d = 1024 with at least one 8-row tile per SM, n x (chunks of E) x C for
+  // smaller batches there, n x E x C at other d.
+  const int64_t need = n > 0 ? logits_scratch_floats(p->L, n, p->E, C, p->num_sms) : 0;
+  if (need > (int64_t)MCK_NOALLOC_MAX_PARTIALS)
+    return fail(MCK_EINVAL, std::to_string(need) +
                                 " partial logits exceed the fixed scratch of " +
                                 std::to_string((int64_t)MCK_NOALLOC_MAX_PARTIALS) +
-                                " (split the batch)");
+                                " floats (split the batch)");
   DeviceScope scope(p->device);
   if (!scope.ok) return fail(MCK_ECUDA, "cannot select the plan's device");
   MCK_TRY(check_x(p, x, n, in_dim, ldx));
