@@ -1,8 +1,8 @@
 """Data-parallel helpers for running the feature map on several GPUs.
 
 Samples are independent and every rank rebuilds the same tables from the
-seed (Sec. "Large-scale Machine Learning": hashing makes the parameters
-reproducible anywhere, which "is crucial for distributed computation"), so
+seed (Sec. "Large-scale Machine Learning": hashed parameters can be
+recreated on any machine, which is what lets the method run distributed), so
 inference shards the batch with no collective at all. Training would sum
 gradients across ranks (``allreduce_grads``).
 """

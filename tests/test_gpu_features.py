@@ -136,14 +136,15 @@ def test_laplace(mck, dev, d, E, n):
     tailed (chi_d over |N(0,1)|), so a few phases are far larger than the
     RBF's: the bar adds, per phase, float32's resolution of z and the
     rounding of the transform, 2^-24 (|z_k| + 4 log2(d) Cs_k max_j |h_j|),
-    with the oracle run on the plan's own float32 Cs (whose parity with the
-    float64 tables is checked with the tables). Phases past 2e5, where float32
-    no longer resolves a period to 1e-5 at all, are only checked to be
-    bounded."""
+    with the oracle's own Cs rounded to float32, the precision the library
+    stores its tables in (the table tests hold the library's Cs to within
+    one float32 ulp of the oracle). Phases past 2e5, where float32 no longer
+    resolves a period to 1e-5 at all, are only checked to be bounded."""
     plan = mck.Plan(d, E, "laplace", 3.0, 2024 + d)
     x = wl.mnist_like(n, min(d, 784), seed=d)
     phi = mck.features(plan, torch.from_numpy(x).to(dev)).cpu().numpy().astype(np.float64)
-    T = dict(_oracle_tables(plan), Cs=plan.tables()["Cs"].astype(np.float64))
+    T = _oracle_tables(plan)
+    T["Cs"] = T["Cs"].astype(np.float32).astype(np.float64)
     z = ff.phases(x.astype(np.float64), T)                      # (n, E, d)
     Cs = T["Cs"][None]
     hmax = np.abs(z / Cs).max(axis=2, keepdims=True)

@@ -10,7 +10,12 @@ times, checked against the FP64 oracle on sampled outputs.
 
 Oracle tables are built only for the sampled outputs' plans and expansions:
 the Matern calibration costs t d^2 draws per expansion on the CPU (about 4 s at
-d = 1024), so config-4 samples use Matern vectors only at d <= 256.
+d = 1024) and the RBF radius one rejection loop per entry, so whole tables are
+built only for small d and few expansions. Larger vectors (Matern above
+d = 256, RBF with E > 24 above d = 1024) are checked at sampled output
+coordinates: each output k of expansion e depends on the calibration only
+through C_e[k], so the oracle runs both transforms with its own B, Pi and G
+and computes C_e[k] for the sampled k alone.
 Bars: features 1e-5 max abs error; logits 1e-4 (sums of 2 E d products).
 """
 
@@ -73,6 +78,80 @@ def test_config1_matern_features_full_size_sampled(mck, dev, mnist):
     ref = ff.features(x[rows].astype(np.float64), _tables(D, 8, ff.MATERN, 3.0, 42))
     assert float(np.abs(got.astype(np.float64) - ref).max()) <= 1e-5
     plan.close()
+
+
+def _oracle_at(xi, d, E, kernel, sigma, seed, ks, t=40):
+    """Oracle features of one vector at output coordinates ks (per expansion
+    e, a list of k) for expansions 0..E-1: both transforms in full with the
+    oracle's B, Pi and G, the calibration only at the sampled k. Returns
+    per-expansion (cos, sin, z, Cs at ks, max_j |h_j|)."""
+    B = ff.table_B(d, E, seed)
+    perm = ff.table_perm(d, E, seed)
+    G = ff.table_G(d, E, seed)
+    gnorm = np.linalg.norm(G, axis=1)
+    out = []
+    for e in range(E):
+        h = ff.stages(xi, B[e], perm[e], G[e], np.ones(d))["h"][0]
+        if kernel == ff.MATERN:
+            r = np.array([ff.ball_sum_norm(d, e, k, t, seed) for k in ks[e]])
+        else:
+            r = np.array([ff.rbf_radius(d, e, k, seed) for k in ks[e]])
+        cs = r / gnorm[e] / (sigma * np.sqrt(d))
+        z = cs * h[ks[e]]
+        out.append((np.cos(z), np.sin(z), z, cs, float(np.abs(h).max())))
+    return out
+
+
+def test_config4_large_vectors_sampled(mck, dev):
+    """The uneven batch's Matern vectors at d = 2^9..2^14 (largest and
+    smallest E at each d) and its RBF vectors with E > 24 at d = 2^11..2^14,
+    at sampled coordinates of every expansion, against the oracle alone.
+    Per-coordinate bar: 1e-5 plus float32's resolution of the phase and the
+    transform's rounding, 2^-24 (|z_k| + 4 log2(d) C_k max_j |h_j|) (phases
+    reach hundreds with N(0,1) entries and sigma = 1)."""
+    b = wl.uneven_batch(10000, seed=42)
+    keys = sorted(set(zip(b["d"].tolist(), b["kernel"].tolist())))
+    plans = [mck.Plan(d, 32, "rbf" if k == 0 else "matern", 1.0, 42, matern_t=40)
+             for d, k in keys]
+    pidx = np.array([keys.index((d, k)) for d, k in zip(b["d"].tolist(), b["kernel"].tolist())])
+    order = np.lexsort((b["E"], b["kernel"], b["d"]))
+    items, x_len, phi_len = mck.group_layout(plans, pidx, b["E"], b["d"], order)
+    xh = np.zeros(x_len, np.float32)
+    for i, v in enumerate(b["x"]):
+        xh[items["x_offset"][i]: items["x_offset"][i] + len(v)] = v
+    g = mck.Group(plans, items, x_len, phi_len)
+    phi = torch.full((phi_len,), float("nan"), device=dev)
+    g.features(torch.from_numpy(xh).to(dev), phi)
+    torch.cuda.synchronize()
+    picks = []
+    for L in range(9, 15):
+        d = 1 << L
+        mat = np.nonzero((b["d"] == d) & (b["kernel"] == 1))[0]
+        if len(mat):
+            picks.append(int(mat[np.argmax(b["E"][mat])]))
+            picks.append(int(mat[np.argmin(b["E"][mat])]))
+        if L >= 11:
+            rbf = np.nonzero((b["d"] == d) & (b["kernel"] == 0) & (b["E"] > 24))[0]
+            if len(rbf):
+                picks.append(int(rbf[np.argmax(b["E"][rbf])]))
+    assert len(picks) >= 14
+    assert max(int(b["E"][i]) for i in picks if b["kernel"][i] == 1 and b["d"][i] >= 4096) > 24
+    rng = np.random.default_rng(7)
+    for i in sorted(set(picks)):
+        d, E, kern = int(b["d"][i]), int(b["E"][i]), int(b["kernel"][i])
+        ks = [sorted({0, d - 1, int(rng.integers(0, d))}) for _ in range(E)]
+        ref = _oracle_at(b["x"][i][None].astype(np.float64), d, E,
+                         ff.RBF if kern == 0 else ff.MATERN, 1.0, 42, ks)
+        o = int(items["phi_offset"][i])
+        got = phi[o: o + 2 * E * d].cpu().numpy().astype(np.float64).reshape(E, 2, d)
+        for e, (c, s_, z, cs, hmax) in enumerate(ref):
+            tol = 1e-5 + 2.0 ** -24 * (np.abs(z) + 4 * np.log2(d) * cs * hmax)
+            err_c = np.abs(got[e, 0, ks[e]] - c)
+            err_s = np.abs(got[e, 1, ks[e]] - s_)
+            assert np.all(err_c <= tol) and np.all(err_s <= tol), \
+                (i, d, E, kern, e, float(err_c.max()), float(err_s.max()), tol)
+    for p in plans:
+        p.close()
 
 
 def test_config4_full_size_sampled(mck, dev):

@@ -5,8 +5,17 @@ rounding of an operand has relative error <= 2^-p (p = 8 for bf16, 11 for fp16
 with round-to-nearest: half an ulp of a p+1-bit significand); an unsplit
 transform rounds twice (the input and the intermediate after the first digit),
 so errors stay near 2^-p; the hi + lo split leaves 2^-2p per rounding. The
-bounds below allow a factor of 4 to 8 over those sizes, far below the O(1)
-error of any wrong index or sign.
+BOUND values allow a factor of 4 to 8 over those sizes, far below the O(1)
+error of any wrong index or sign: they are regression bounds of the error
+model, one per form, not the accuracy target.
+
+The accuracy target for the 16-bit forms is a max abs error of 2e-3 on the
+orthonormal output (error relative to sqrt(d) rms(x), as measured here).
+FP16 unsplit and both hi + lo forms meet it (test_north_star_bar).
+BF16 unsplit does NOT meet it: rounding the input to 8 significant bits alone
+leaves 2^-9 relative error per element, about 1.1e-3 rms after the transform
+and ~5e-3 at the maximum over millions of outputs (1.2e-2 measured at
+d = 1024). No test claims that bar for BF16 unsplit.
 """
 
 import numpy as np
@@ -18,7 +27,12 @@ from oracle import fastfood as ff
 
 pytestmark = pytest.mark.gpu
 
+# Error-model regression bounds (see the module docstring), not the target.
 BOUND = {"bf16": 2.0 ** -6, "fp16": 2.0 ** -8, "bf16_split": 2.0 ** -14, "fp16_split": 2.0 ** -18}
+# The target's max abs error for the 16-bit forms; BF16 unsplit is excluded
+# because it cannot meet it (module docstring).
+NORTH_STAR_BAR = 2e-3
+MEETS_BAR = ("fp16", "bf16_split", "fp16_split")
 
 
 def _rel_err(got, x):
@@ -84,3 +98,16 @@ def test_tensor_core_rejects_unsupported_shapes(mck, dev):
         mck.fwht_(torch.zeros((8, 128), device=dev), "bf16")
     with pytest.raises(mck.MckError, match="multiple of 1024"):
         mck.fwht_(torch.zeros((3, 256), device=dev), "bf16")
+
+
+@pytest.mark.parametrize("prec", MEETS_BAR)
+@pytest.mark.parametrize("L,n", [(10, 4096), (14, 256), (20, 4)])
+def test_north_star_bar(mck, dev, L, n, prec):
+    """The 2e-3 max abs error target on many outputs (2^22 at d = 1024 and
+    2^14, 2^22 at 2^20) for the forms that meet it."""
+    d = 1 << L
+    x = wl.gaussian(n, d, seed=100 + L)
+    t = torch.from_numpy(x).to(dev)
+    mck.fwht_(t, prec)
+    err = _rel_err(t.cpu().numpy(), x)
+    assert err <= NORTH_STAR_BAR, (d, prec, err)

@@ -67,6 +67,26 @@ def test_matern_tables(mck, d, E, t):
     plan.close()
 
 
+@pytest.mark.parametrize("d,E", [(1 << 11, 32), (1 << 13, 4), (1 << 14, 32), (1 << 15, 2)])
+def test_matern_tables_large_d(mck, d, E):
+    """Matern calibration above d = 1024 (the uneven batch builds t = 40
+    plans up to 2^14 with 32 expansions): sampled entries (e, k) against the
+    oracle's literal ball sum (t d normals per entry), the radius over
+    ||G_e|| and sigma sqrt d; float32 ball coordinates bound the agreement
+    to 2e-6 relative."""
+    sigma, t, seed = 1.0, 40, 42
+    plan = mck.Plan(d, E, "matern", sigma, seed, matern_t=t)
+    tab = plan.tables()
+    plan.close()
+    es = sorted({0, E // 2, E - 1})
+    ks = sorted({0, 1, 511, d // 2 + 3, d - 1} | set(np.random.default_rng(d).integers(0, d, 2).tolist()))
+    G = ff.table_G(d, E, seed=seed)
+    r = ff.table_radius(d, E, ff.MATERN, t, seed=seed, ks=ks)
+    expect = r / np.linalg.norm(G, axis=1, keepdims=True) / (sigma * np.sqrt(d))
+    np.testing.assert_allclose(tab["Cs"][np.ix_(es, ks)], expect[es], rtol=2e-6, atol=0)
+    assert np.all(tab["Cs"] > 0) and np.isfinite(tab["Cs"]).all()
+
+
 def test_seed_determinism_and_independence(mck):
     a = mck.Plan(256, 2, "rbf", 1.0, 99).tables()
     b = mck.Plan(256, 2, "rbf", 1.0, 99).tables()
