@@ -27,7 +27,9 @@ Reported:
                a power-of-2 batch (N = 2^16)
   feature_sweep the batched feature kernels at d = 2^5..2^15
   cpu_baseline the FP64 oracle on a bounded sample of the same workload, one
-               spawned process per host core (the single-core figure inside)
+               spawned process per host core (the single-core figure inside),
+               and the plain FP32 C program (cpu_baseline/) on every host core
+               over the whole batch, with the host CPU model
 
 --impl reference times the oracle itself (CPU, every host core) on the same
 workload, as the reference arm.
@@ -240,6 +242,38 @@ def cpu_baseline_all_cores(rows_per_core=CPU_SAMPLE_ROWS // 2):
             "sample": f"{rows_per_core * cores} rows ({rows_per_core} per process), float64 numpy, {dt:.1f} s"}
 
 
+def cpu_baseline_fp32(T, reps=3):
+    """The plain FP32 CPU program (cpu_baseline/: iterative in-place FP32
+    transform and feature map, samples split over POSIX threads) on every
+    host core, over the whole 60000-row batch, each feature written to a
+    2048-row wrap-around host buffer. Tables: the oracle's generator, rounded
+    to float32. Best of `reps` passes; accuracy checked on 4 rows against
+    the oracle."""
+    import cpu_baseline as cb
+    import workloads as wl
+    from oracle import fastfood as ff
+
+    tabs = (T["B"].astype(np.float32), T["perm"].astype(np.uint32),
+            T["G"].astype(np.float32), T["Cs"].astype(np.float32))
+    x = wl.mnist_like(N, IN_DIM, seed=SEED)
+    out = np.empty((2048, F), np.float32)
+    cores = os.cpu_count() or 1
+    cb.features(x[:64], *tabs, threads=cores, out=out)  # load and fault in
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        cb.features(x, *tabs, threads=cores, out=out)
+        times.append(time.perf_counter() - t0)
+    dt = min(times)
+    chk = cb.features(x[:4], *tabs, threads=1)
+    T32 = dict(T, G=tabs[2].astype(np.float64), Cs=tabs[3].astype(np.float64))
+    err = float(np.abs(chk - ff.features(x[:4].astype(np.float64), T32)).max())
+    return {"value": N * F / dt, "unit": "features/s", "cores": cores, "kind": "plain_fp32_c",
+            "gbs": N * (IN_DIM + F) * 4 / dt / 1e9, "seconds": dt,
+            "sample": f"the whole {N}-row batch (d={D}, E={E}), float32 C, {cores} POSIX threads, "
+                      f"best of {reps}", "max_abs_err_vs_oracle_4_rows": err}
+
+
 def cpu_baseline(rows=CPU_SAMPLE_ROWS):
     """The FP64 oracle (as it stands, single thread) on `rows` rows of the workload."""
     import workloads as wl
@@ -406,12 +440,22 @@ def main():
             line["configs01"] = configs01_leg(mck, dev, stream, args)
     del phi
     if rank == 0 and world == 1 and not args.no_extras:
+        import cpu_baseline as cb
+        from oracle import fastfood as ff
+
         one = cpu_baseline()
         try:
             line["cpu_baseline"] = cpu_baseline_all_cores()
             line["cpu_baseline"]["single_core"] = one
         except Exception as exc:  # a host without process spawning: one core only
             line["cpu_baseline"] = dict(one, all_cores_error=f"{type(exc).__name__}: {exc}"[:160])
+        line["cpu_baseline"]["cpu_model"] = cb.cpu_model()
+        try:
+            line["cpu_baseline"]["plain_fp32_all_cores"] = cpu_baseline_fp32(
+                ff.plan_tables(D, E, ff.RBF, SIGMA, seed=SEED))
+        except Exception as exc:
+            line["cpu_baseline"]["plain_fp32_all_cores"] = {
+                "error": f"{type(exc).__name__}: {exc}"[:160]}
     elif rank == 0:
         line["cpu_baseline"] = None
     if rank == 0:
