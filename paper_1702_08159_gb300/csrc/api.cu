@@ -146,6 +146,8 @@ FeatureArgs feature_args(const mck_plan_s* p, const float* x, int64_t n, int64_t
   a.permB = p->permB;
   a.GB = G ? nullptr : p->GB;  // an overriding G is read in natural order
   a.maskA = p->maskA;
+  a.permS = p->permS;
+  a.ubase = p->ubase;
   a.E = p->E;
   a.L = p->L;
   a.num_sms = p->num_sms;
@@ -267,6 +269,9 @@ mck_status_t mck_plan_ex(mck_plan_t* out, int64_t d, int32_t E, int32_t kernel, 
          cudaMalloc(&p->GB, sizeof(float) * n) == cudaSuccess &&
          cudaMalloc(&p->maskA, sizeof(uint32_t) * T * E) == cudaSuccess;
   }
+  if (ok && p->L == 10)
+    ok = cudaMalloc(&p->permS, sizeof(uint32_t) * n / 2) == cudaSuccess &&
+         cudaMalloc(&p->ubase, sizeof(uint32_t) * 32 * E) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     mck_plan_destroy(p);
@@ -277,8 +282,9 @@ mck_status_t mck_plan_ex(mck_plan_t* out, int64_t d, int32_t E, int32_t kernel, 
     mck_plan_destroy(p);
     return cuda_fail(err, "cudaStreamCreate");
   }
-  const mck_status_t st = build_tables(p, s);
+  mck_status_t st = build_tables(p, s);
   cudaStreamDestroy(s);
+  if (st == MCK_OK) st = build_skew_tables(p);
   if (st != MCK_OK) {
     mck_plan_destroy(p);
     return st;
@@ -304,6 +310,8 @@ void mck_plan_destroy(mck_plan_t p) {
     cudaFree(p->permB);
     cudaFree(p->GB);
     cudaFree(p->maskA);
+    cudaFree(p->permS);
+    cudaFree(p->ubase);
     cudaGetLastError();
   }
   delete p;

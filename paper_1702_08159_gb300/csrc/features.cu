@@ -60,6 +60,27 @@ __device__ __forceinline__ void apply_signs(float (&w)[32], uint32_t mask) {
     w[j] = __int_as_float(__float_as_int(w[j]) ^ ((mask << (31 - j)) & 0x80000000u));
 }
 
+// d = 1024: u into the skewed slot for the Pi gather (register j at word
+// base + 33 j; see mck_plan_s::permS), and the lane's 16 packed gather
+// offsets (byte offsets of registers 2i and 2i + 1 in the halves of word i).
+__device__ __forceinline__ void store_skew(float* buf, uint32_t base, const float (&w)[32]) {
+  float* q = buf + base;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) q[33 * j] = w[j];
+}
+__device__ __forceinline__ void load_skew_offsets(const uint32_t* __restrict__ permS, int lam,
+                                                  uint32_t (&poff)[16]) {
+  const uint4* ps = reinterpret_cast<const uint4*>(permS) + lam;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint4 v = __ldg(ps + q * 32);
+    poff[4 * q] = v.x;
+    poff[4 * q + 1] = v.y;
+    poff[4 * q + 2] = v.z;
+    poff[4 * q + 3] = v.w;
+  }
+}
+
 // B bits of the elements of layout A held by thread lam, as a 32-bit mask.
 template <int L>
 __device__ __forceinline__ uint32_t load_bmask_A(const uint32_t* __restrict__ Bw, int lam) {
@@ -228,6 +249,7 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_FEATURES ? kWarpMinB
   float gt[32], cs[32];
   uint32_t poff[16];  // gather byte offsets inside the slot, two 16-bit values each
   uint32_t pslot = 0;
+  uint32_t ubase = 0;  // d = 1024: this lane's word base in the skewed slot
   int cur_e = -1;
 
   for (int64_t it = it0; it < it1; ++it) {
@@ -250,12 +272,17 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_FEATURES ? kWarpMinB
       const uint32_t slot = buf_addr + 4u * (uint32_t)(g * Y::SLOT);
       // Gather offsets are below 2^16 bytes: two per register.
       pslot = slot;
-      const uint4* pb = reinterpret_cast<const uint4*>(P.a.permB + off) + lam;
+      if constexpr (L == 10) {  // skewed slot, offsets packed at plan time
+        ubase = __ldg(P.a.ubase + (int64_t)e * 32 + lam);
+        load_skew_offsets(P.a.permS + (int64_t)e * (d / 2), lam, poff);
+      } else {
+        const uint4* pb = reinterpret_cast<const uint4*>(P.a.permB + off) + lam;
 #pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const uint4 v = __ldg(pb + m * Y::T);
-        poff[2 * m] = v.x | (v.y << 16);
-        poff[2 * m + 1] = v.z | (v.w << 16);
+        for (int m = 0; m < 8; ++m) {
+          const uint4 v = __ldg(pb + m * Y::T);
+          poff[2 * m] = v.x | (v.y << 16);
+          poff[2 * m + 1] = v.z | (v.w << 16);
+        }
       }
       if (P.a.GB) {
         const float4* gb = reinterpret_cast<const float4*>(P.a.GB + off) + lam;
@@ -310,7 +337,8 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_FEATURES ? kWarpMinB
       }
       hreg<Y::maskB()>(w);
       // v = Pi u: u goes to shared memory, each register gathers its source.
-      store_B<L>(buf, g, lam, w);
+      if constexpr (L == 10) store_skew(buf, ubase, w);
+      else store_B<L>(buf, g, lam, w);
       __syncwarp();
 #pragma unroll
       for (int j = 0; j < 32; ++j)
@@ -656,7 +684,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_logits_tile(const Launch P,
   constexpr int TPG = kConsumers / CG;  // consumer threads per class group
   constexpr int ITER = F24 / TPG;       // float4 columns per consumer thread and expansion
   static_assert(Y::SLOT <= F2 && F24 % TPG == 0 && TPG % 32 == 0, "tile shape");
-  static_assert(kTileRows * 12 == 3 * (d / 32), "8 producer warps x 12 lines cover permB, G and Cs");
+  static_assert(kTileRows * 10 == (d / 2 + 2 * d) / 32, "8 producer warps x 10 lines cover permS, G and Cs");
   extern __shared__ float4 sm4[];
   float* phis = reinterpret_cast<float*>(sm4);  // [2][kTileRows][F2]
   float* red = phis + 2 * kTileRows * F2;       // [8 consumer warps][kTileRows][CPT]
@@ -682,28 +710,23 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_logits_tile(const Launch P,
         float* buf = phis + (bsel * kTileRows + warp) * F2;
         const uint32_t slot = smem_addr(buf);
         const int64_t off = (int64_t)e * d;
-        {  // the next step's tables (permB, G, Cs: 96 lines of 128 B) into L1, 12 per warp
+        {  // the next step's tables (permS, G, Cs: 80 lines of 128 B) into L1, 10 per warp
           const int64_t offn = (int64_t)(e + 1 < E ? e + 1 : 0) * d;
-          if (lane < 12) {
-            const int li = warp * 12 + lane;
+          if (lane < 10) {
+            const int li = warp * 10 + lane;
             const float* gsrc = P.a.GB ? P.a.GB : P.a.G;
             const char* line =
-                li < 32   ? reinterpret_cast<const char*>(P.a.permB + offn) + li * 128
-                : li < 64 ? reinterpret_cast<const char*>(gsrc + offn) + (li - 32) * 128
-                          : reinterpret_cast<const char*>(P.a.Cs + offn) + (li - 64) * 128;
+                li < 16   ? reinterpret_cast<const char*>(P.a.permS + offn / 2) + li * 128
+                : li < 48 ? reinterpret_cast<const char*>(gsrc + offn) + (li - 16) * 128
+                          : reinterpret_cast<const char*>(P.a.Cs + offn) + (li - 48) * 128;
             asm volatile("prefetch.global.L1 [%0];" ::"l"(line));
           }
         }
         const uint32_t bmask = __ldg(P.a.maskA + (int64_t)e * Y::T + lane);
+        const uint32_t ubase = __ldg(P.a.ubase + (int64_t)e * 32 + lane);
         uint32_t poff[16];
         float gt[32];
-        const uint4* pb = reinterpret_cast<const uint4*>(P.a.permB + off) + lane;
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const uint4 v = __ldg(pb + m * Y::T);
-          poff[2 * m] = v.x | (v.y << 16);
-          poff[2 * m + 1] = v.z | (v.w << 16);
-        }
+        load_skew_offsets(P.a.permS + (int64_t)e * (d / 2), lane, poff);
         if (P.a.GB) {
           const float4* gb = reinterpret_cast<const float4*>(P.a.GB + off) + lane;
 #pragma unroll
@@ -726,7 +749,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_logits_tile(const Launch P,
         __syncwarp();
         load_B<L>(buf, 0, lane, w);
         hreg<Y::maskB()>(w);
-        store_B<L>(buf, 0, lane, w);
+        store_skew(buf, ubase, w);
         __syncwarp();
 #pragma unroll
         for (int j = 0; j < 32; ++j)

@@ -32,6 +32,13 @@ struct mck_plan_s {
   uint32_t* permB = nullptr;   // E x d
   float* GB = nullptr;         // E x d: G_e[k]
   uint32_t* maskA = nullptr;   // E x d/32: bit j set where B_e[kA(lam, j)] = -1
+  // d = 1024 only, for the forward warp kernels: u = H B x-hat is stored for
+  // the Pi gather in a skewed slot (register j of lane lam at word
+  // ubase[e][lam] + 33 j, so a store instruction is conflict free for any
+  // per-lane bases), and the bases are chosen at plan time to spread each
+  // gather instruction's 32 sources over the 32 banks.
+  uint32_t* permS = nullptr;   // E x d/2: gather byte offsets into the skewed slot, two 16-bit per word
+  uint32_t* ubase = nullptr;   // E x 32: word base of lane lam's registers in the skewed slot
 };
 
 namespace mck {
@@ -44,6 +51,9 @@ mck_status_t check_device_array(const void* p, int64_t bytes, int device, const 
 
 // ---- plan.cu -------------------------------------------------------------
 mck_status_t build_tables(mck_plan_s* p, cudaStream_t s);
+// d = 1024: the skewed gather tables (permS, ubase) from the plan's Pi (host
+// search per expansion; synchronous). No-op for other d.
+mck_status_t build_skew_tables(mck_plan_s* p);
 // Replace the plan's signs: B_e[k] = -1 where B[e][k] < 0 (device E x d
 // floats), and rebuild the lane-ordered tables that hold them (stream-ordered).
 cudaError_t set_signs(mck_plan_s* p, const float* B, cudaStream_t s);
@@ -70,6 +80,8 @@ struct FeatureArgs {
   const uint32_t* permB;  // lane-ordered tables (warp kernels); null when absent
   const float* GB;        // null when G is overridden by the caller
   const uint32_t* maskA;
+  const uint32_t* permS;  // d = 1024: skewed gather tables (see mck_plan_s); null when absent
+  const uint32_t* ubase;
   int32_t E;
   int L;
   int num_sms;

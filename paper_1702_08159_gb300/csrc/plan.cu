@@ -10,8 +10,12 @@
 // last-place differences of log/cos).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -402,6 +406,170 @@ mck_status_t build_tables(mck_plan_s* p, cudaStream_t s) {
   if (err != cudaSuccess) return cuda_fail(err, "plan kernels");
   err = cudaStreamSynchronize(s);
   if (err != cudaSuccess) return cuda_fail(err, "plan kernels");
+  return MCK_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Skewed gather tables for d = 1024 (a memory layout of the forward warp
+// kernels; the paper's method is unchanged by it).
+//
+// The forward kernels hold u = H B x-hat in layout B (lane lam, register j:
+// element kB(lam, j)) and gather v_k = u_{pi(k)} for the same layout, one
+// shared-memory load per register: load j of lane lam reads element
+// pi(kB(lam, j)). With u stored in natural order these 32 reads of a warp hit
+// random banks (about 3.5 times the conflict-free cost). Here u is stored with
+// register j of lane lam at word base[lam] + 33 j: a store instruction (one j,
+// all lanes) then touches banks (base[lam] + j) mod 32, distinct for any
+// permutation `base` of 0..31, and the gather's banks become
+// (base[lane of the source] + register of the source) mod 32. The bases of
+// each expansion are chosen by simulated annealing over swaps, minimising the
+// gather's wavefronts (the sum over its 32 loads of the largest number of
+// lanes that share a bank); with random permutations this takes the gather
+// from ~112 to ~84 wavefronts. The search is seeded by (plan seed,
+// expansion), so equal plans get equal tables.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct SplitMix {
+  uint64_t s;
+  uint64_t next() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  double unit() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+};
+
+// Lane and register of element s in layout B at d = 1024.
+inline int lane_of(int s) { return (s & 3) | ((s >> 7) << 2); }
+inline int reg_of(int s) { return (s >> 2) & 31; }
+
+// Bases (a permutation of 0..31) for one expansion's permutation pi (1024
+// entries); returns the gather's wavefront count with them.
+int skew_bases(const uint32_t* pi, uint64_t seed, int iters, uint8_t* base) {
+  // The 32 sources read from each lane group a: (load j, register of source).
+  int occ_j[32][32], occ_r[32][32], nocc[32] = {0};
+  for (int l = 0; l < 32; ++l)
+    for (int j = 0; j < 32; ++j) {
+      const int src = (int)pi[Lay<10>::kB(l, j)];
+      const int a = lane_of(src);
+      occ_j[a][nocc[a]] = j;
+      occ_r[a][nocc[a]] = reg_of(src);
+      ++nocc[a];
+    }
+  int f[32], best_f[32];
+  for (int a = 0; a < 32; ++a) f[a] = a;
+  // cnt[j][b]: lanes of load j reading bank b; hist[j][c]: banks with count
+  // c; mx[j]: the largest count (the load's wavefronts).
+  int cnt[32][32], hist[32][34], mx[32];
+  std::memset(cnt, 0, sizeof cnt);
+  std::memset(hist, 0, sizeof hist);
+  for (int a = 0; a < 32; ++a)
+    for (int i = 0; i < nocc[a]; ++i) cnt[occ_j[a][i]][(f[a] + occ_r[a][i]) & 31]++;
+  for (int j = 0; j < 32; ++j) {
+    mx[j] = 0;
+    for (int b = 0; b < 32; ++b) {
+      hist[j][cnt[j][b]]++;
+      if (cnt[j][b] > mx[j]) mx[j] = cnt[j][b];
+    }
+  }
+  auto inc = [&](int j, int b) {
+    const int c = cnt[j][b]++;
+    hist[j][c]--;
+    hist[j][c + 1]++;
+    if (c + 1 > mx[j]) mx[j] = c + 1;
+  };
+  auto dec = [&](int j, int b) {
+    const int c = cnt[j][b]--;
+    hist[j][c]--;
+    hist[j][c - 1]++;
+    if (hist[j][mx[j]] == 0) mx[j]--;
+  };
+  auto total = [&] {
+    int t = 0;
+    for (int j = 0; j < 32; ++j) t += mx[j];
+    return t;
+  };
+  auto swap_bases = [&](int a, int b) {
+    for (int i = 0; i < nocc[a]; ++i) {
+      dec(occ_j[a][i], (f[a] + occ_r[a][i]) & 31);
+      inc(occ_j[a][i], (f[b] + occ_r[a][i]) & 31);
+    }
+    for (int i = 0; i < nocc[b]; ++i) {
+      dec(occ_j[b][i], (f[b] + occ_r[b][i]) & 31);
+      inc(occ_j[b][i], (f[a] + occ_r[b][i]) & 31);
+    }
+    const int t = f[a];
+    f[a] = f[b];
+    f[b] = t;
+  };
+  SplitMix rng{seed};
+  int cur = total(), best = cur;
+  std::memcpy(best_f, f, sizeof f);
+  for (int it = 0; it < iters; ++it) {
+    const double T = 2.0 * (1.0 - (double)it / iters) + 0.01;  // linear cooling
+    const int a = (int)(rng.next() & 31), b = (int)((rng.next() >> 8) & 31);
+    if (a == b) continue;
+    swap_bases(a, b);
+    const int c = total();
+    if (c <= cur || rng.unit() < std::exp((cur - c) / T)) {
+      cur = c;
+      if (c < best) {
+        best = c;
+        std::memcpy(best_f, f, sizeof f);
+      }
+    } else {
+      swap_bases(a, b);
+    }
+  }
+  for (int a = 0; a < 32; ++a) base[a] = (uint8_t)best_f[a];
+  return best;
+}
+
+constexpr int kSkewIters = 20000;
+
+}  // namespace
+
+mck_status_t build_skew_tables(mck_plan_s* p) {
+  if (p->L != 10 || !p->permS || !p->ubase) return MCK_OK;
+  const int d = 1024;
+  const int64_t E = p->E;
+  std::vector<uint32_t> pi((size_t)E * d), permS((size_t)E * d / 2), ubase((size_t)E * 32);
+  cudaError_t err = cudaMemcpy(pi.data(), p->perm, sizeof(uint32_t) * pi.size(), cudaMemcpyDeviceToHost);
+  if (err != cudaSuccess) return cuda_fail(err, "plan: skewed gather tables");
+  auto work = [&](int64_t e) {
+    uint8_t base[32];
+    skew_bases(pi.data() + e * d, p->seed ^ (0x5851F42D4C957F2Dull * (uint64_t)(e + 1)), kSkewIters,
+               base);
+    for (int l = 0; l < 32; ++l) ubase[(size_t)e * 32 + l] = base[l];
+    // Lane lam's 16 packed words: word i holds the byte offsets of its
+    // registers 2i (low half) and 2i + 1 (high half); stored as 4 x uint4
+    // per lane, uint4 q of lane lam at (q * 32 + lam).
+    for (int lam = 0; lam < 32; ++lam)
+      for (int i = 0; i < 16; ++i) {
+        uint32_t wv = 0;
+        for (int h = 0; h < 2; ++h) {
+          const int src = (int)pi[(size_t)e * d + Lay<10>::kB(lam, 2 * i + h)];
+          const uint32_t off = 4u * (uint32_t)(base[lane_of(src)] + 33 * reg_of(src));
+          wv |= off << (16 * h);
+        }
+        permS[(size_t)e * (d / 2) + ((size_t)(i >> 2) * 32 + lam) * 4 + (i & 3)] = wv;
+      }
+  };
+  const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(E, std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (int64_t t = 1; t < nt; ++t)
+    pool.emplace_back([&, t] {
+      for (int64_t e = t; e < E; e += nt) work(e);
+    });
+  for (int64_t e = 0; e < E; e += nt) work(e);
+  for (auto& th : pool) th.join();
+  err = cudaMemcpy(p->permS, permS.data(), sizeof(uint32_t) * permS.size(), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess)
+    err = cudaMemcpy(p->ubase, ubase.data(), sizeof(uint32_t) * ubase.size(), cudaMemcpyHostToDevice);
+  if (err != cudaSuccess) return cuda_fail(err, "plan: skewed gather tables");
   return MCK_OK;
 }
 
