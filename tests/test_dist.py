@@ -72,3 +72,65 @@ def test_two_rank_gloo():
         assert mx == 2.5                        # max over ranks
         assert total == 60001
         assert grad == [3.0, 3.0, 3.0]          # 1 + 2
+
+
+class _SoftmaxRegression(torch.nn.Module):
+    """A stand-in with the classifier's training interface (parameters and
+    a mean cross-entropy loss) in plain torch, so the data-parallel host
+    logic of sgd.fit runs on CPU ranks."""
+
+    def __init__(self, dim, classes):
+        super().__init__()
+        g = torch.Generator().manual_seed(0)
+        self.W = torch.nn.Parameter(0.1 * torch.randn(classes, dim, generator=g, dtype=torch.float64))
+        self.b = torch.nn.Parameter(torch.zeros(classes, dtype=torch.float64))
+
+    def loss(self, x, y):
+        return torch.nn.functional.cross_entropy(x.double() @ self.W.T + self.b, y.long())
+
+
+def _data():
+    g = torch.Generator().manual_seed(1)
+    x = torch.randn(53, 6, generator=g)
+    y = torch.randint(0, 4, (53,), generator=g, dtype=torch.int32)
+    return x, y
+
+
+def _fit_worker(rank, world, port, q):
+    from paper_1702_08159_gb300.sgd import fit
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        x, y = _data()
+        m = _SoftmaxRegression(6, 4)
+        hist = fit(m, x, y, lr=0.5, batch=5, epochs=3, seed=7)  # last batch of 3: one rank gets 1 row
+        q.put((rank, m.W.detach().numpy(), m.b.detach().numpy(), hist))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_data_parallel_fit_matches_one_process():
+    """Two gloo ranks each take half of every mini-batch and sum weighted
+    gradients: both end with the parameters, and the epoch losses, of one
+    process training on the whole mini-batches."""
+    from paper_1702_08159_gb300.sgd import fit
+
+    x, y = _data()
+    ref = _SoftmaxRegression(6, 4)
+    ref_hist = fit(ref, x, y, lr=0.5, batch=5, epochs=3, seed=7)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_fit_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for _, W, b, hist in out:
+        assert abs(W - ref.W.detach().numpy()).max() < 1e-12
+        assert abs(b - ref.b.detach().numpy()).max() < 1e-12
+        assert max(abs(h - r) for h, r in zip(hist, ref_hist)) < 1e-12
