@@ -352,6 +352,11 @@ def main():
         if world > 1:
             dist.barrier(device_ids=[local])
 
+    # The plan's launch shape, picked by the autotuner on this batch (every
+    # shape gives the same bits); timed outside the measured region.
+    from paper_1702_08159_gb300 import tune
+
+    shape, shape_ms, _ = tune.tune_features(plan, x, out=phi, reps=3)
     for _ in range(args.warmup):
         mck.features(plan, x, out=phi)
     torch.cuda.synchronize()
@@ -413,6 +418,8 @@ def main():
                            parallelism=f"dp{world} (samples sharded, no collective)"),
             "hbm_gbs": world * nb * bytes_per_row * args.steps / (ms / 1e3) / 1e9,
             "roofline": roofline, "clocks": clk.summary(), "gpu_launches": args.steps,
+            "launch_shape": {"rows_per_item": shape[0], "staged": shape[1],
+                             "tuned_ms": {f"{k[0]},{k[1]}": v for k, v in shape_ms.items()}},
             "launch_ms": {"mean": statistics.mean(launch_ms), "min": min(launch_ms),
                           "max": max(launch_ms)}}
 
@@ -581,9 +588,16 @@ def fwht_sweep_leg(mck, dev, stream, args):
                 times.append(a.elapsed_time(b))
         ms = statistics.mean(times)
         gbs = 8.0 * total / (ms / 1e3) / 1e9
-        out.append({"d": d, "batch": n, "ms": ms, "gbs": gbs, "frac_of_measured_hbm": gbs / peak,
-                    "passes": 1 if L <= 17 else 2, "max_err_rel_sqrt_d_rms": rel,
-                    "err_rows": rows})
+        rec = {"d": d, "batch": n, "ms": ms, "gbs": gbs, "frac_of_measured_hbm": gbs / peak,
+               "passes": 1 if L <= 17 else 2, "max_err_rel_sqrt_d_rms": rel, "err_rows": rows}
+        if L in (16, 17):  # the tunable regime: every candidate's time on this batch
+            from paper_1702_08159_gb300 import tune
+
+            work.copy_(x0)
+            best, regime_ms, _ = tune.tune_fwht(work.view(n, d), reps=3)
+            rec["regimes_ms"] = regime_ms
+            rec["tuned_regime"] = best
+        out.append(rec)
     # Tensor-core Kronecker-H16 forms (16-bit operands, FP32 accumulation) at
     # every d of the sweep: the tensor cores on each 1024-float block, FP32
     # column passes for the index bits above 10 when d > 1024.
@@ -685,6 +699,7 @@ def feature_sweep_leg(mck, dev, stream, args):
     import torch
 
     import workloads as wl
+    from paper_1702_08159_gb300 import tune
 
     out = []
     for L in range(5, 16):
@@ -693,20 +708,28 @@ def feature_sweep_leg(mck, dev, stream, args):
         plan = mck.Plan(d, E, "rbf", 1.0, SEED)
         x = torch.from_numpy(wl.gaussian(n, d, seed=SEED + L)).to(dev)
         phi = torch.empty((n, 2 * E * d), device=dev)
-        for _ in range(3):
-            mck.features(plan, x, out=phi)
-        torch.cuda.synchronize()
-        reps = 5
-        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(reps):
-            mck.features(plan, x, out=phi)
-        e.record(stream)
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(e) / reps
+
+        def timed():
+            for _ in range(3):
+                mck.features(plan, x, out=phi)
+            torch.cuda.synchronize()
+            reps = 5
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                mck.features(plan, x, out=phi)
+            e.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(e) / reps
+
+        ms_auto = timed()
+        shape, shape_ms, _ = tune.tune_features(plan, x, out=phi, reps=3)
+        ms = timed()
         gbs = n * (d + 2 * E * d) * 4 / (ms / 1e3) / 1e9
         out.append({"d": d, "E": E, "rows": n, "ms": ms, "gbs": gbs,
-                    "frac_of_measured_hbm": gbs / measured_peaks()[0]})
+                    "frac_of_measured_hbm": gbs / measured_peaks()[0],
+                    "ms_automatic_shape": ms_auto, "tuned_shape": list(shape),
+                    "tuned_ms": {f"{k[0]},{k[1]}": v for k, v in shape_ms.items()}})
         plan.close()
         del x, phi
     return out
@@ -724,8 +747,14 @@ def uneven_leg(mck, dev, stream, args):
 
     b = wl.uneven_batch(args.uneven_count, seed=SEED)
     keys = sorted(set(zip(b["d"].tolist(), b["kernel"].tolist())))
-    plans = [mck.Plan(d, 32, "rbf" if k == 0 else "matern", 1.0, SEED, matern_t=40)
-             for d, k in keys]
+    plans, plan_s = [], {}
+    for d, k in keys:
+        # plan creation is synchronous (tables on the device, the skewed
+        # gather search on the host at d = 1024); the Matern calibration costs
+        # t d^2 normals per expansion
+        t0 = time.perf_counter()
+        plans.append(mck.Plan(d, 32, "rbf" if k == 0 else "matern", 1.0, SEED, matern_t=40))
+        plan_s[f"{'rbf' if k == 0 else 'matern'}_d{d}"] = time.perf_counter() - t0
     pidx = np.array([keys.index((d, k)) for d, k in zip(b["d"].tolist(), b["kernel"].tolist())])
     order = np.lexsort((b["E"], b["kernel"], b["d"]))
     items, x_len, phi_len = mck.group_layout(plans, pidx, b["E"], b["d"], order)
@@ -776,7 +805,8 @@ def uneven_leg(mck, dev, stream, args):
            "features_per_s_persistent": feats / (ms_graph / 1e3),
            "speedup_vs_per_class": ms_per_class / ms_graph,
            "gb_per_s_written": 4.0 * feats / (ms_graph / 1e3) / 1e9,
-           "max_abs_diff_vs_per_class": same, "info": g.info()}
+           "max_abs_diff_vs_per_class": same, "info": g.info(),
+           "plan_create_s_E32": plan_s}
     del phi, phi_b, x, cap, groups, g
     for pl in plans:
         pl.close()

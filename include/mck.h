@@ -35,7 +35,9 @@
  * - Every call returns an mck_status_t. On failure mck_last_error() gives a
  *   message for the calling thread. Argument errors are detected before any
  *   device work is queued. MCK_ECUDA reports a CUDA runtime error.
- * - Sizes: 2 <= d <= 2^15 for plans; n >= 0 (n = 0 is a no-op).
+ * - Sizes: 2 <= d <= 2^20 for plans (Matern: d <= 2^15); n >= 0 (n = 0 is a
+ *   no-op). Above d = 2^15 the features run in passes over HBM scratch
+ *   (stream-ordered, at most 256 MiB); see mck_features.
  */
 #ifndef MCK_H
 #define MCK_H
@@ -73,14 +75,15 @@ typedef enum {
   MCK_FP16_SPLIT = 4  /* fp16 with the hi + lo split */
 } mck_prec_t;
 
-#define MCK_MAX_LOG2_D 15          /* largest plan dimension: d = 2^15 */
+#define MCK_MAX_LOG2_D 20          /* largest plan dimension: d = 2^20 */
+#define MCK_MAX_LOG2_D_MATERN 15   /* largest Matern plan: d = 2^15 (t d^2 draws per expansion) */
 #define MCK_MAX_LOG2_D_FWHT 20     /* largest standalone transform: d = 2^20 */
 #define MCK_MAX_CLASSES 16         /* largest class count of the fused logit kernels */
 
 /* Create a plan: the tables B, Pi, G and C of E expansions of dimension d,
  * recreated from `seed` (Sec. "McKernel" items B, Pi, G, C; Sec. "API
  * Description": factory pattern, parameters from a hash).
- *   d       padded dimension, a power of two, 2 <= d <= 2^15
+ *   d       padded dimension, a power of two, 2 <= d <= 2^20 (Matern: <= 2^15)
  *   E       number of expansions, 1 <= E <= 65536
  *   kernel  MCK_RBF, MCK_MATERN or MCK_LAPLACE
  *   sigma   kernel width, finite and > 0 (the sigma of Eq. etn:mckernel)
@@ -89,7 +92,8 @@ typedef enum {
  * captions). The plan is created on the current CUDA device. The call is
  * synchronous: the tables are ready when it returns. *out is set only on
  * success. Errors: MCK_EINVAL (bad argument, NULL out), MCK_EUNSUPPORTED
- * (d > 2^15), MCK_ENOMEM, MCK_ECUDA. */
+ * (d > 2^20, or a Matern plan above 2^15), MCK_ENOMEM, MCK_ECUDA. For
+ * d > 2^15 the permutations are drawn on the host (the same draws and swaps). */
 mck_status_t mck_plan(mck_plan_t* out, int64_t d, int32_t E, int32_t kernel, double sigma,
                       uint64_t seed);
 
@@ -113,6 +117,26 @@ mck_status_t mck_plan_info(mck_plan_t plan, int64_t* d, int32_t* E, int32_t* ker
  *   Cs      E x d float32: C/(sigma sqrt d) (Eq. etn:mckernel) */
 mck_status_t mck_plan_tables(mck_plan_t plan, uint32_t* B_bits, uint32_t* perm, float* G,
                              float* Cs);
+
+/* Launch shape of the batched feature kernels (mck_features, and
+ * mck_fused_logits at d != 1024) for this plan: a tunable. Every shape gives
+ * bit-identical results; paper_1702_08159_gb300/tune.py picks the fastest per
+ * workload.
+ *   rows_per_item  samples one work item covers with one load of an
+ *                  expansion's tables. 0 = automatic. 32 <= d <= 1024:
+ *                  32 / (d / 32) (one round of the warp's vectors, at least 1)
+ *                  or max(4, that) (a full tile). 2^11 <= d <= 2^14: 1, 2 or 4.
+ *   staged         -1 = automatic, 0 = off, 1 = on: the block copies the next
+ *                  row's input and the expansion's Cs into shared memory with
+ *                  cp.async ahead of use (2^11 <= d <= 2^14; rows that are not
+ *                  16-byte aligned with in_dim % 4 == 0 run unstaged).
+ * Other values, or anything but (0, -1) at other d, return MCK_EINVAL. Host
+ * only: calls queued afterwards use the new shape; do not change it while
+ * another thread launches work with the plan. */
+mck_status_t mck_plan_set_launch(mck_plan_t plan, int32_t rows_per_item, int32_t staged);
+
+/* The plan's launch shape (as set; 0 / -1 = automatic); outputs may be NULL. */
+mck_status_t mck_plan_get_launch(mck_plan_t plan, int32_t* rows_per_item, int32_t* staged);
 
 /* Replace the plan's sign diagonals B (Sec. "Empirical Analysis": learning
  * B, which the paper likens to attention; a trainer keeps real values and
@@ -142,16 +166,37 @@ mck_status_t mck_plan_set_signs(mck_plan_t plan, const float* B, mck_stream_t st
  *         (MCK_EUNSUPPORTED / MCK_EINVAL otherwise). */
 mck_status_t mck_fwht(float* x, int64_t n, int64_t d, int32_t prec, mck_stream_t stream);
 
+/* How the FP32 transform runs at d = 2^16 and 2^17 (a tunable: every regime
+ * gives bit-identical results; see paper_1702_08159_gb300/tune.py). */
+typedef enum {
+  MCK_FWHT_AUTO = 0,          /* the library's choice (MCK_FWHT_CLUSTER_2_15) */
+  MCK_FWHT_CLUSTER_2_15 = 1,  /* one pass, a thread-block cluster of 2 or 4 blocks of 2^15 */
+  MCK_FWHT_CLUSTER_2_14 = 2,  /* one pass, a cluster of 4 or 8 blocks of 2^14 */
+  MCK_FWHT_TWO_PASS = 3       /* 2^15-float blocks, then a column pass over HBM */
+} mck_fwht_regime_t;
+
+/* mck_fwht with the regime for d = 2^16, 2^17 (prec must be MCK_FP32 there
+ * when regime != MCK_FWHT_AUTO; at other d only MCK_FWHT_AUTO is accepted).
+ * Errors as mck_fwht, plus MCK_EINVAL for an unknown or inapplicable regime. */
+mck_status_t mck_fwht_ex(float* x, int64_t n, int64_t d, int32_t prec, int32_t regime,
+                         mck_stream_t stream);
+
 /* phi = features of n samples (Eq. etn:mckernel, Eq. etn:mcfeatures).
  *   x       device n x in_dim (ld ldx), 1 <= in_dim <= d; padded with zeros to d
  *   Cs, G   device E x d or NULL (plan tables)
- *   phi     device n x (2 E d), 16-byte aligned; row = E blocks of [cos | sin] */
+ *   phi     device n x (2 E d), 16-byte aligned; row = E blocks of [cos | sin]
+ * d <= 2^15 runs fused kernels (phi is the only output traffic). Above 2^15
+ * the map runs in passes (signs, transform, gather with G, transform, Cs and
+ * [cos | sin]) over stream-ordered scratch of at most 256 MiB, rows in
+ * chunks. */
 mck_status_t mck_features(mck_plan_t plan, const float* x, int64_t n, int64_t in_dim,
                           int64_t ldx, const float* Cs, const float* G, float* phi,
                           mck_stream_t stream);
 
 /* Gradients of sum(phi(x) * dphi) (the adjoint of mck_features, with H^T = H
  * and Pi^T = Pi^{-1}; the forward is recomputed, nothing is stored).
+ * 32 <= d <= 2^20: fused kernels up to d = 1024, passes over stream-ordered
+ * scratch (at most 256 MiB) above; MCK_EUNSUPPORTED below 32.
  *   dphi  device n x (2 E d)
  *   dx    device n x in_dim (ld ldx) or NULL
  *   dCs   device E x d or NULL: sum over samples of h * dz
@@ -179,7 +224,8 @@ mck_status_t mck_features_backward_ex(mck_plan_t plan, const float* x, int64_t n
  *   logits   device n x num_classes
  * 1 <= num_classes <= MCK_MAX_CLASSES. Uses stream-ordered scratch memory of
  * at most n x E x num_classes floats for partial logits (none at d = 1024
- * when the batch has at least 8 rows per SM). */
+ * when the batch has at least 8 rows per SM). Above d = 2^15 the features of
+ * the rows in flight go to scratch (at most 256 MiB) before the contraction. */
 mck_status_t mck_fused_logits(mck_plan_t plan, const float* x, int64_t n, int64_t in_dim,
                               int64_t ldx, const float* Cs, const float* G, const float* W,
                               const float* b, int32_t num_classes, float* logits,

@@ -126,6 +126,29 @@ class Plan:
         check(load().mck_plan_set_signs(self.handle, _ptr(B), _stream(B.device)),
               "mck_plan_set_signs")
 
+    def set_launch(self, rows_per_item=0, staged=-1):
+        """Launch shape of the batched feature kernels (mck_plan_set_launch):
+        0 / -1 = automatic; results are identical for every shape."""
+        check(load().mck_plan_set_launch(self.handle, int(rows_per_item), int(staged)),
+              "mck_plan_set_launch")
+
+    def launch(self):
+        """(rows_per_item, staged) as set (0 / -1 = automatic)."""
+        r, st = ctypes.c_int32(), ctypes.c_int32()
+        check(load().mck_plan_get_launch(self.handle, ctypes.byref(r), ctypes.byref(st)),
+              "mck_plan_get_launch")
+        return r.value, st.value
+
+    def launch_candidates(self):
+        """Every accepted (rows_per_item, staged) shape of this plan's d."""
+        L = self.d.bit_length() - 1
+        if 5 <= L <= 10:
+            vpw = 32 // (1 << (L - 5))
+            return sorted({(vpw, -1), (max(4, vpw), -1)})
+        if 11 <= L <= 14:
+            return [(r, st) for r in (1, 2, 4) for st in (0, 1)]
+        return [(0, -1)]
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             load().mck_plan_destroy(self._h)
@@ -153,12 +176,14 @@ def _tables(plan, Cs, G):
     return Cs, G
 
 
-def fwht_(x, prec="fp32"):
+def fwht_(x, prec="fp32", regime="auto"):
     """In-place unnormalised Walsh-Hadamard transform of the rows of x (last dim d).
 
-    prec: "fp32" (float32 butterflies, any d <= 2^20) or, for d in {256, 512,
-    1024}, the tensor-core Kronecker-H16 forms "bf16", "fp16", "bf16_split",
+    prec: "fp32" (float32 butterflies, any d <= 2^20) or, for 256 <= d <= 2^20,
+    the tensor-core Kronecker-H16 forms "bf16", "fp16", "bf16_split",
     "fp16_split" (16-bit operands, FP32 accumulation; *_split = hi + lo).
+    regime (FP32 at d = 2^16, 2^17 only): "auto", "cluster_2_15",
+    "cluster_2_14" or "two_pass" (mck_fwht_ex; identical results).
     """
     _f32_cuda(x, "x")
     if not x.is_contiguous():
@@ -166,8 +191,9 @@ def fwht_(x, prec="fp32"):
     d = x.size(-1)
     n = x.numel() // d if d else 0
     p = _lib.PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    r = _lib.FWHT_REGIMES[regime] if isinstance(regime, str) else int(regime)
     with torch.cuda.device(x.device):
-        check(load().mck_fwht(_ptr(x), n, d, p, _stream(x.device)), "mck_fwht")
+        check(load().mck_fwht_ex(_ptr(x), n, d, p, r, _stream(x.device)), "mck_fwht_ex")
     return x
 
 

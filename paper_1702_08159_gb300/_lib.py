@@ -25,8 +25,10 @@ MCK_FP16 = 2
 MCK_BF16_SPLIT = 3
 MCK_FP16_SPLIT = 4
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16_split": 3, "fp16_split": 4}
+FWHT_REGIMES = {"auto": 0, "cluster_2_15": 1, "cluster_2_14": 2, "two_pass": 3}
 
-MAX_LOG2_D = 15
+MAX_LOG2_D = 20
+MAX_LOG2_D_MATERN = 15
 MAX_LOG2_D_FWHT = 20
 MAX_CLASSES = 16
 
@@ -48,6 +50,9 @@ SIGNATURES = {
     "mck_plan_tables": (_ST, [_P, _P, _P, _P, _P]),
     "mck_plan_set_signs": (_ST, [_P, _P, _P]),
     "mck_fwht": (_ST, [_P, _I64, _I64, _I32, _P]),
+    "mck_fwht_ex": (_ST, [_P, _I64, _I64, _I32, _I32, _P]),
+    "mck_plan_set_launch": (_ST, [_P, _I32, _I32]),
+    "mck_plan_get_launch": (_ST, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "mck_features": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P]),
     "mck_features_backward": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, _P]),
     "mck_features_backward_ex": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, _P,

@@ -148,6 +148,8 @@ FeatureArgs feature_args(const mck_plan_s* p, const float* x, int64_t n, int64_t
   a.maskA = p->maskA;
   a.permS = p->permS;
   a.ubase = p->ubase;
+  a.rows_per_item = p->rows_per_item;
+  a.staged = p->staged;
   a.E = p->E;
   a.L = p->L;
   a.num_sms = p->num_sms;
@@ -227,7 +229,10 @@ mck_status_t mck_plan_ex(mck_plan_t* out, int64_t d, int32_t E, int32_t kernel, 
   if (!out) return fail(MCK_EINVAL, "out is NULL");
   if (!is_pow2(d) || d < 2) return fail(MCK_EINVAL, "d must be a power of two >= 2");
   if (d > ((int64_t)1 << MCK_MAX_LOG2_D))
-    return fail(MCK_EUNSUPPORTED, "plans support d <= 2^15");
+    return fail(MCK_EUNSUPPORTED, "plans support d <= 2^20");
+  if (kernel == MCK_MATERN && d > ((int64_t)1 << MCK_MAX_LOG2_D_MATERN))
+    return fail(MCK_EUNSUPPORTED, "Matern plans support d <= 2^15 (the ball sum draws t d^2 "
+                                  "normals per expansion)");
   if (E < 1 || E > 65536) return fail(MCK_EINVAL, "E must be in [1, 65536]");
   if ((int64_t)E * d > ((int64_t)1 << 28)) return fail(MCK_EINVAL, "E * d must be <= 2^28");
   if (kernel != MCK_RBF && kernel != MCK_MATERN && kernel != MCK_LAPLACE) return fail(MCK_EINVAL, "unknown kernel");
@@ -330,6 +335,33 @@ mck_status_t mck_plan_info(mck_plan_t p, int64_t* d, int32_t* E, int32_t* kernel
   return MCK_OK;
 }
 
+mck_status_t mck_plan_set_launch(mck_plan_t p, int32_t rows_per_item, int32_t staged) {
+  MCK_TRY(check_plan(p));
+  if (staged < -1 || staged > 1) return fail(MCK_EINVAL, "staged must be -1, 0 or 1");
+  if (p->L >= 5 && p->L <= 10) {
+    const int T = 1 << (p->L - 5), vpw = 32 / T, spi = vpw >= 4 ? vpw : 4;
+    if (rows_per_item != 0 && rows_per_item != vpw && rows_per_item != spi)
+      return fail(MCK_EINVAL, "rows_per_item at this d must be 0, " + std::to_string(vpw) +
+                                  " or " + std::to_string(spi));
+    if (staged != -1) return fail(MCK_EINVAL, "staging applies to 2^11 <= d <= 2^14 only");
+  } else if (p->L >= 11 && p->L <= 14) {
+    if (rows_per_item != 0 && rows_per_item != 1 && rows_per_item != 2 && rows_per_item != 4)
+      return fail(MCK_EINVAL, "rows_per_item at this d must be 0, 1, 2 or 4");
+  } else if (rows_per_item != 0 || staged != -1) {
+    return fail(MCK_EINVAL, "this d has one launch shape (rows_per_item 0, staged -1)");
+  }
+  p->rows_per_item = rows_per_item;
+  p->staged = staged;
+  return MCK_OK;
+}
+
+mck_status_t mck_plan_get_launch(mck_plan_t p, int32_t* rows_per_item, int32_t* staged) {
+  MCK_TRY(check_plan(p));
+  if (rows_per_item) *rows_per_item = p->rows_per_item;
+  if (staged) *staged = p->staged;
+  return MCK_OK;
+}
+
 mck_status_t mck_plan_tables(mck_plan_t p, uint32_t* B_bits, uint32_t* perm, float* G, float* Cs) {
   MCK_TRY(check_plan(p));
   DeviceScope scope(p->device);
@@ -345,7 +377,15 @@ mck_status_t mck_plan_tables(mck_plan_t p, uint32_t* B_bits, uint32_t* perm, flo
 }
 
 mck_status_t mck_fwht(float* x, int64_t n, int64_t d, int32_t prec, mck_stream_t stream) {
+  return mck_fwht_ex(x, n, d, prec, MCK_FWHT_AUTO, stream);
+}
+
+mck_status_t mck_fwht_ex(float* x, int64_t n, int64_t d, int32_t prec, int32_t regime,
+                         mck_stream_t stream) {
   if (prec < MCK_FP32 || prec > MCK_FP16_SPLIT) return fail(MCK_EUNSUPPORTED, "unknown precision");
+  if (regime < MCK_FWHT_AUTO || regime > MCK_FWHT_TWO_PASS) return fail(MCK_EINVAL, "unknown regime");
+  if (regime != MCK_FWHT_AUTO && (prec != MCK_FP32 || (d != (1 << 16) && d != (1 << 17))))
+    return fail(MCK_EINVAL, "a transform regime can be chosen only for FP32 at d = 2^16 or 2^17");
   if (!is_pow2(d)) return fail(MCK_EINVAL, "d must be a power of two");
   if (prec != MCK_FP32 && !fwht_mma_supported(log2i(d)))
     return fail(MCK_EUNSUPPORTED, "the tensor-core transform supports 256 <= d <= 2^20");
@@ -363,7 +403,8 @@ mck_status_t mck_fwht(float* x, int64_t n, int64_t d, int32_t prec, mck_stream_t
   if (prec != MCK_FP32)
     return launched(launch_fwht_mma(x, n, log2i(d), prec, sm_count(device), (cudaStream_t)stream),
                     "mck_fwht");
-  return launched(launch_fwht(x, n, log2i(d), sm_count(device), (cudaStream_t)stream), "mck_fwht");
+  return launched(launch_fwht(x, n, log2i(d), sm_count(device), (cudaStream_t)stream, regime),
+                  "mck_fwht");
 }
 
 mck_status_t mck_features(mck_plan_t p, const float* x, int64_t n, int64_t in_dim, int64_t ldx,
@@ -376,14 +417,26 @@ mck_status_t mck_features(mck_plan_t p, const float* x, int64_t n, int64_t in_di
   if (n == 0) return MCK_OK;
   MCK_TRY(check_array(phi, 4 * n * F, p->device, "phi"));
   if (p->d >= 4 && (uintptr_t)phi % 16) return fail(MCK_EINVAL, "phi must be 16-byte aligned");
-  return launched(launch_features(feature_args(p, x, n, in_dim, ldx, Cs, G), phi,
-                                  (cudaStream_t)stream),
+  cudaStream_t s = (cudaStream_t)stream;
+  if (p->L > 15) {  // multi-pass over a scratch of the rows in flight
+    Scratch sc(s);
+    MCK_TRY(sc.alloc(sizeof(float) * (size_t)multipass_scratch_floats(p->L, n, p->E, 0, false)));
+    return launched(launch_features_multipass(feature_args(p, x, n, in_dim, ldx, Cs, G), phi,
+                                              nullptr, nullptr, 0, nullptr, (float*)sc.ptr, s),
+                    "mck_features");
+  }
+  return launched(launch_features(feature_args(p, x, n, in_dim, ldx, Cs, G), phi, s),
                   "mck_features");
 }
 
 static mck_status_t run_backward(mck_plan_s* p, BackwardArgs b, cudaStream_t s, const char* who) {
   const int64_t n = b.f.n;
   if (n == 0) return MCK_OK;
+  if (p->L > 10) {  // multi-pass adjoint
+    Scratch sc(s);
+    MCK_TRY(sc.alloc(sizeof(float) * (size_t)multipass_scratch_floats(p->L, n, p->E, 0, true)));
+    return launched(launch_backward_multipass(b, (float*)sc.ptr, s), who);
+  }
   const bool params = b.dCs || b.dG || b.dB || b.phi_out;
   const int64_t np = params ? backward_partials(p->L, n, p->E, p->num_sms) : 0;
   Scratch part(s);
@@ -396,7 +449,7 @@ mck_status_t mck_features_backward_ex(mck_plan_t p, const float* x, int64_t n, i
                                       const float* dphi, float* dx, float* dCs, float* dG,
                                       float* dB, mck_stream_t stream) {
   MCK_TRY(check_plan(p));
-  if (p->L < 5 || p->L > 10) return fail(MCK_EUNSUPPORTED, "the adjoint supports 32 <= d <= 1024");
+  if (p->L < 5) return fail(MCK_EUNSUPPORTED, "the adjoint supports 32 <= d <= 2^20");
   DeviceScope scope(p->device);
   MCK_TRY(check_x(p, x, n, in_dim, ldx));
   MCK_TRY(check_tables(p, Cs, G));
@@ -459,7 +512,7 @@ mck_status_t mck_fused_logits_backward_ex(mck_plan_t p, const float* x, int64_t 
                                           const float* dlogits, float* dx, float* dCs, float* dG,
                                           float* dB, float* dW, float* db, mck_stream_t stream) {
   MCK_TRY(check_plan(p));
-  if (p->L < 5 || p->L > 10) return fail(MCK_EUNSUPPORTED, "the adjoint supports 32 <= d <= 1024");
+  if (p->L < 5) return fail(MCK_EUNSUPPORTED, "the adjoint supports 32 <= d <= 2^20");
   if (C < 1 || C > MCK_MAX_CLASSES) return fail(MCK_EINVAL, "num_classes must be in [1, 16]");
   DeviceScope scope(p->device);
   MCK_TRY(check_x(p, x, n, in_dim, ldx));

@@ -366,28 +366,65 @@ __device__ __forceinline__ void chunk_columns_inplace(float* sm, int tid) {
   }
 }
 
-// The whole feature map of one vector-expansion in the chunked block form.
-// Tables are the expansion's (offset by e d): Pi as shared-memory word
-// offsets and G lane-ordered per chunk (GB), or G in natural order (Gnat)
-// when the caller overrides it; the B masks per (chunk, lane); Cs natural.
-// `out` receives [cos z | sin z] (2d floats). `bar` synchronises the NT
-// threads of the (sub-)block.
+// The tables a warp of the chunked block form holds for its chunk of one
+// expansion: the B mask of its lanes, the Pi word offsets (packed two per
+// register) and G (lane-ordered, or natural order when overridden).
+struct ChunkTabs {
+  uint32_t bmask;
+  uint32_t poff[16];
+  float gt[32];
+};
+
+template <int L>
+__device__ __forceinline__ void load_chunk_tabs(const uint32_t* __restrict__ permB,
+                                                const float* __restrict__ GB,
+                                                const float* __restrict__ Gnat,
+                                                const uint32_t* __restrict__ maskA, int tid,
+                                                ChunkTabs& t) {
+  using Y = Lay<10>;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int co = warp * 1024;
+  t.bmask = __ldg(maskA + warp * 32 + lane);
+  const uint4* pb = reinterpret_cast<const uint4*>(permB + co) + lane;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const uint4 v = __ldg(pb + m * 32);
+    t.poff[2 * m] = v.x | (v.y << 16);
+    t.poff[2 * m + 1] = v.z | (v.w << 16);
+  }
+  if (Gnat) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) t.gt[j] = __ldg(Gnat + co + Y::kB(lane, j));
+  } else {
+    const float4* gb = reinterpret_cast<const float4*>(GB + co) + lane;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const float4 v = __ldg(gb + m * 32);
+      t.gt[4 * m] = v.x;
+      t.gt[4 * m + 1] = v.y;
+      t.gt[4 * m + 2] = v.z;
+      t.gt[4 * m + 3] = v.w;
+    }
+  }
+}
+
+// The whole feature map of one vector-expansion in the chunked block form,
+// with the expansion's tables already in registers (`t`, see
+// load_chunk_tabs); Cs natural order (offset by e d). `out` receives
+// [cos z | sin z] (2d floats). `bar` synchronises the NT threads of the
+// (sub-)block.
 // STAGED: the caller has copied x-hat into shared memory with cp.async (xs:
 // this warp's 1024-float chunk, zero past in_dim, in one commit group that
-// it has waited for) and Cs (css: the expansion's d values, in the commit
-// group before the one `next` makes). The warp reads its chunk, then calls
-// `next` (which queues the next item's copies into xs); the output stage
-// waits for the Cs group.
+// it has waited for) and Cs (css: the expansion's d values, in a commit
+// group no later than the one before `next`'s). The warp reads its chunk,
+// then calls `next` (which queues the next row's copies into xs); the
+// output stage waits for all but the newest commit group.
 template <int L, bool STAGED, class Bar, class Next>
-__device__ __forceinline__ void chunked_map_impl(const float* __restrict__ xrow, int64_t in_dim,
-                                                 bool vec_x, const uint32_t* __restrict__ permB,
-                                                 const float* __restrict__ GB,
-                                                 const float* __restrict__ Gnat,
-                                                 const uint32_t* __restrict__ maskA,
-                                                 const float* __restrict__ cs,
-                                                 float* __restrict__ out, float* sm, int tid,
-                                                 Bar bar, const float* xs, const float* css,
-                                                 Next next) {
+__device__ __forceinline__ void chunked_body(const ChunkTabs& t, const float* __restrict__ xrow,
+                                             int64_t in_dim, bool vec_x,
+                                             const float* __restrict__ cs,
+                                             float* __restrict__ out, float* sm, int tid, Bar bar,
+                                             const float* xs, const float* css, Next next) {
   using C = Chunked<L>;
   using Y = Lay<10>;
   constexpr int d = 1 << L;
@@ -395,32 +432,7 @@ __device__ __forceinline__ void chunked_map_impl(const float* __restrict__ xrow,
   float* slot = sm + warp * C::SLOT;
   const uint32_t sbase = smem_addr(sm);
   const int co = warp * 1024;
-  const uint32_t bmask = __ldg(maskA + warp * 32 + lane);
-  uint32_t poff[16];
-  float gt[32];
-  {
-    const uint4* pb = reinterpret_cast<const uint4*>(permB + co) + lane;
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const uint4 v = __ldg(pb + m * 32);
-      poff[2 * m] = v.x | (v.y << 16);
-      poff[2 * m + 1] = v.z | (v.w << 16);
-    }
-    if (Gnat) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) gt[j] = __ldg(Gnat + co + Y::kB(lane, j));
-    } else {
-      const float4* gb = reinterpret_cast<const float4*>(GB + co) + lane;
-#pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const float4 v = __ldg(gb + m * 32);
-        gt[4 * m] = v.x;
-        gt[4 * m + 1] = v.y;
-        gt[4 * m + 2] = v.z;
-        gt[4 * m + 3] = v.w;
-      }
-    }
-  }
+  const uint32_t bmask = t.bmask;
   // u = H B x-hat: index bits 0..9 per warp, then 10..L-1 across the chunks
   {
     float w[32];
@@ -473,8 +485,8 @@ __device__ __forceinline__ void chunked_map_impl(const float* __restrict__ xrow,
   float w[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j)
-    w[j] = lds32(sbase + 4u * ((j & 1) ? (poff[j >> 1] >> 16) : (poff[j >> 1] & 0xffffu)));
-  hreg_scaled<Y::maskB()>(w, gt);
+    w[j] = lds32(sbase + 4u * ((j & 1) ? (t.poff[j >> 1] >> 16) : (t.poff[j >> 1] & 0xffffu)));
+  hreg_scaled<Y::maskB()>(w, t.gt);
   bar();  // every warp has gathered: the slots may be rewritten
   store_B<10>(slot, 0, lane, w);
   __syncwarp();
@@ -482,7 +494,7 @@ __device__ __forceinline__ void chunked_map_impl(const float* __restrict__ xrow,
   hreg<Y::maskA()>(w);
   __syncwarp();
   store_A<10>(slot, 0, lane, w);
-  if constexpr (STAGED) cp_async_wait<1>();  // this thread's Cs copies have landed
+  if constexpr (STAGED) cp_async_wait<1>();  // this thread's Cs copies have landed (older group)
   bar();
   // bits 10..L-1 of the second transform, then z = Cs h and [cos | sin]
 #pragma unroll
@@ -529,6 +541,7 @@ __device__ __forceinline__ void chunked_map_impl(const float* __restrict__ xrow,
   bar();  // the slots (and Cs) are read before the next item rewrites them
 }
 
+// Tables and map together (one vector-expansion).
 template <int L, class Bar>
 __device__ __forceinline__ void chunked_map(const float* __restrict__ xrow, int64_t in_dim,
                                             bool vec_x, const uint32_t* __restrict__ permB,
@@ -537,8 +550,9 @@ __device__ __forceinline__ void chunked_map(const float* __restrict__ xrow, int6
                                             const uint32_t* __restrict__ maskA,
                                             const float* __restrict__ cs, float* __restrict__ out,
                                             float* sm, int tid, Bar bar) {
-  chunked_map_impl<L, false>(xrow, in_dim, vec_x, permB, GB, Gnat, maskA, cs, out, sm, tid, bar,
-                             nullptr, nullptr, [] {});
+  ChunkTabs t;
+  load_chunk_tabs<L>(permB, GB, Gnat, maskA, tid, t);
+  chunked_body<L, false>(t, xrow, in_dim, vec_x, cs, out, sm, tid, bar, nullptr, nullptr, [] {});
 }
 
 }  // namespace mck

@@ -463,91 +463,6 @@ __global__ void __launch_bounds__(1 << (L - 5)) k_feat_cta(const Launch P) {
 }
 
 // ---------------------------------------------------------------------------
-// Chunked block kernel, 11 <= L <= 14 (features): one block of W = 2^(L-10)
-// warps per (sample, expansion) item, expansions fastest; the chunked form
-// described in common.cuh, with the chunk tables made at plan time (B mask,
-// Pi word offsets packed two per register, G) and Cs read at the output.
-// ---------------------------------------------------------------------------
-template <int L>
-__device__ __forceinline__ void chunked_item(const Launch& P, int64_t n, int e, float* sm, int tid,
-                                             const float* __restrict__ Gov) {
-  constexpr int d = 1 << L;
-  const int64_t eo = (int64_t)e * d;
-  chunked_map<L>(P.a.x + n * P.a.ldx, P.a.in_dim, P.vec_x, P.a.permB + eo,
-                 Gov ? nullptr : P.a.GB + eo, Gov ? Gov + eo : nullptr, P.a.maskA + eo / 32,
-                 P.a.Cs + eo, P.phi + n * 2ll * P.a.E * d + 2ll * e * d, sm, tid,
-                 [] { __syncthreads(); });
-}
-
-template <int L>  // 16 warps per SM at 128 registers (measured best; 64 registers spill)
-__global__ void __launch_bounds__(Chunked<L>::NT, 512 / Chunked<L>::NT) k_feat_chunks(const Launch P) {
-  extern __shared__ float4 sm4[];
-  float* sm = reinterpret_cast<float*>(sm4);
-  const int E = P.a.E;
-  const int64_t items = P.a.n * E;
-  const float* Gov = P.a.GB ? nullptr : P.a.G;
-  for (int64_t it = blockIdx.x; it < items; it += gridDim.x)
-    chunked_item<L>(P, it / E, (int)(it % E), sm, threadIdx.x, Gov);
-}
-
-// The same with the input staged: each block copies the next item's x-hat
-// (its warps' chunks) and the current item's Cs into shared memory with
-// cp.async, so neither load is waited for in the item's critical path (the
-// block holds one item at a time and every warp starts it together). Needs
-// 16-byte aligned rows with in_dim % 4 == 0 (vec_x); shared memory: the
-// chunk slots plus 2 d floats. Used at d = 2^14.
-template <int L>
-__global__ void __launch_bounds__(Chunked<L>::NT, 512 / Chunked<L>::NT)
-    k_feat_chunks_staged(const Launch P) {
-  using C = Chunked<L>;
-  constexpr int d = 1 << L;
-  extern __shared__ float4 sm4[];
-  float* sm = reinterpret_cast<float*>(sm4);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  float* xs = sm + C::WORDS + warp * 1024;  // this warp's chunk of x-hat
-  float* css = sm + C::WORDS + d;           // Cs of the item's expansion
-  const int E = P.a.E;
-  const int64_t items = P.a.n * E;
-  const float* Gov = P.a.GB ? nullptr : P.a.G;
-  // One commit group per call: the warp's chunk of item `it` (none past the end).
-  auto copy_x = [&](int64_t it) {
-    if (it < items) {
-      const float* row = P.a.x + (it / E) * P.a.ldx;
-#pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const int c = 4 * (lane + 32 * m);
-        const int64_t k = (int64_t)warp * 1024 + c;
-        const bool in = k < P.a.in_dim;
-        cp_async16(smem_addr(xs + c), in ? row + k : row, in ? 16 : 0);
-      }
-    }
-    cp_async_commit();
-  };
-  int64_t it = blockIdx.x;
-  copy_x(it);
-  for (; it < items; it += gridDim.x) {
-    const int64_t n = it / E;
-    const int e = (int)(it % E);
-    const int64_t eo = (int64_t)e * d;
-    cp_async_wait<0>();  // this thread's copies of the item's x-hat
-    const float* cs = P.a.Cs + eo;
-#pragma unroll
-    for (int j = 0; j < d / (4 * C::NT); ++j) {
-      const int q = 4 * (tid + C::NT * j);
-      cp_async16(smem_addr(css + q), cs + q, 16);
-    }
-    cp_async_commit();
-    const int64_t next = it + gridDim.x;
-    chunked_map_impl<L, true>(nullptr, P.a.in_dim, true, P.a.permB + eo,
-                              Gov ? nullptr : P.a.GB + eo, Gov ? Gov + eo : nullptr,
-                              P.a.maskA + eo / 32, nullptr,
-                              P.phi + n * 2ll * E * d + 2ll * e * d, sm, tid,
-                              [] { __syncthreads(); }, xs, css, [&] { copy_x(next); });
-  }
-  cp_async_wait<0>();
-}
-
-// ---------------------------------------------------------------------------
 // Thread kernel, 1 <= L <= 4: one thread per (n, e), everything in registers.
 // ---------------------------------------------------------------------------
 template <int L>
@@ -914,7 +829,10 @@ cudaError_t run(const Launch& P, cudaStream_t s) {
     const int64_t slots = (int64_t)num_sms * occ * kWarps;  // resident warps
     const int64_t full = (P.a.n + WS::SPI - 1) / WS::SPI * P.a.E;
     if constexpr (WS::R > 1) {
-      if (full < slots) {  // a small batch: one round of VPW samples per item
+      // One round of VPW samples per item: chosen by the plan's launch shape,
+      // else for a small batch (fewer full tiles than resident warps).
+      const bool one = P.a.rows_per_item > 0 ? P.a.rows_per_item == WS::VPW : full < slots;
+      if (one) {
         const int64_t items = (P.a.n + WS::VPW - 1) / WS::VPW * P.a.E;
         const unsigned grid = (unsigned)std::max<int64_t>(
             1, std::min<int64_t>((items + kWarps - 1) / kWarps, slots / kWarps));
@@ -926,32 +844,7 @@ cudaError_t run(const Launch& P, cudaStream_t s) {
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, slots / kWarps));
     k_feat_warp<L, MODE><<<grid, kWarps * 32, 0, s>>>(P);
   } else if constexpr (MODE == MODE_FEATURES && L <= 14) {
-    // Staging pays at 2^14 only, where one block per SM leaves nothing to
-    // hide the loads (2^14: 0.491 -> 0.449 ms in the feature sweep); with two
-    // or more blocks per SM (2^11..2^13) the extra shared-memory traffic made
-    // it 7% slower.
-    if constexpr (L == 14) {
-      if (P.vec_x && (reinterpret_cast<uintptr_t>(P.a.Cs) % 16) == 0) {
-        const size_t smem = sizeof(float) * (Chunked<L>::WORDS + 2 * (1 << L));
-        cudaError_t err = cudaFuncSetAttribute(k_feat_chunks_staged<L>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        const int occ = occ_blocks(k_feat_chunks_staged<L>, Chunked<L>::NT, smem);
-        const int64_t items = P.a.n * P.a.E;
-        const unsigned grid =
-            (unsigned)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)num_sms * occ));
-        k_feat_chunks_staged<L><<<grid, Chunked<L>::NT, smem, s>>>(P);
-        return cudaGetLastError();
-      }
-    }
-    const size_t smem = sizeof(float) * Chunked<L>::WORDS;
-    cudaError_t err = cudaFuncSetAttribute(k_feat_chunks<L>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    const int occ = occ_blocks(k_feat_chunks<L>, Chunked<L>::NT, smem);
-    const int64_t items = P.a.n * P.a.E;
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)num_sms * occ));
-    k_feat_chunks<L><<<grid, Chunked<L>::NT, smem, s>>>(P);
+    return launch_chunked_features(P.a, P.vec_x, P.phi, s);
   } else {
     const size_t smem = sizeof(float) * Lay<L>::SLOT;
     cudaError_t err = cudaFuncSetAttribute(k_feat_cta<L, MODE>,
@@ -999,12 +892,14 @@ Launch make_launch(const FeatureArgs& a) {
 
 cudaError_t launch_features(const FeatureArgs& a, float* phi, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
+  if (a.L > 15) return cudaErrorInvalidValue;  // multi-pass: launch_features_multipass
   Launch P = make_launch(a);
   P.phi = phi;
   return dispatch<MODE_FEATURES>(P, s);
 }
 
 int64_t logits_scratch_floats(int L, int64_t n, int E, int C, int num_sms) {
+  if (L > 15) return multipass_scratch_floats(L, n, E, C, false);
   if (L != 10) return n * E * C;
   const int ec = logits_echunks(n, E, num_sms);
   return ec > 1 ? n * ec * C : 0;
@@ -1013,6 +908,8 @@ int64_t logits_scratch_floats(int L, int64_t n, int E, int C, int num_sms) {
 cudaError_t launch_logits(const FeatureArgs& a, const float* W, const float* b, int C,
                           float* part, float* logits, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
+  if (a.L > 15)  // multi-pass: `part` is the scratch for the chunk's features
+    return launch_features_multipass(a, nullptr, W, b, C, logits, part, s);
   Launch P = make_launch(a);
   P.W = W;
   P.part = part;

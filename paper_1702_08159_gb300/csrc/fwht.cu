@@ -372,7 +372,7 @@ cudaError_t launch_fwht_high_bits(float* x, int64_t n, int L, int num_sms, cudaS
   }
 }
 
-cudaError_t launch_fwht(float* x, int64_t n, int L, int num_sms, cudaStream_t s) {
+cudaError_t launch_fwht(float* x, int64_t n, int L, int num_sms, cudaStream_t s, int regime) {
   if (n == 0 || L == 0) return cudaSuccess;
   switch (L) {
     case 1: return run_tiny<1>(x, n, num_sms, s);
@@ -394,10 +394,15 @@ cudaError_t launch_fwht(float* x, int64_t n, int L, int num_sms, cudaStream_t s)
   }
   if (L > 20) return cudaErrorInvalidValue;
   // One pass on a cluster of 2 or 4 blocks of 2^15 (54% and 49% of the copy
-  // bandwidth, against 33% and 37% for two passes); a cluster of 8 whole-SM
-  // blocks packs the GPCs poorly and measured slower than two passes.
-  if (L == 16) return run_cluster<15, 2>(x, n, s);
-  if (L == 17) return run_cluster<15, 4>(x, n, s);
+  // bandwidth, against 33% and 37% for two passes) unless the caller picks
+  // another regime (MCK_FWHT_CLUSTER_2_14: clusters of 4 or 8 blocks of 2^14,
+  // MCK_FWHT_TWO_PASS); a cluster of 8 whole-SM blocks packs the GPCs poorly
+  // and measured slower than two passes.
+  if (L <= 17 && regime != MCK_FWHT_TWO_PASS) {
+    if (regime == MCK_FWHT_CLUSTER_2_14)
+      return L == 16 ? run_cluster<14, 4>(x, n, s) : run_cluster<14, 8>(x, n, s);
+    return L == 16 ? run_cluster<15, 2>(x, n, s) : run_cluster<15, 4>(x, n, s);
+  }
   const int64_t blocks = n << (L - 15);
   cudaError_t err = run_chunks<15>(x, blocks, num_sms, s);
   if (err != cudaSuccess) return err;

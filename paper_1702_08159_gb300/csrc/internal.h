@@ -39,6 +39,9 @@ struct mck_plan_s {
   // gather instruction's 32 sources over the 32 banks.
   uint32_t* permS = nullptr;   // E x d/2: gather byte offsets into the skewed slot, two 16-bit per word
   uint32_t* ubase = nullptr;   // E x 32: word base of lane lam's registers in the skewed slot
+  // Launch shape of the batched feature kernels (mck_plan_set_launch).
+  int32_t rows_per_item = 0;   // 0 = automatic
+  int32_t staged = -1;         // -1 = automatic
 };
 
 namespace mck {
@@ -59,7 +62,9 @@ mck_status_t build_skew_tables(mck_plan_s* p);
 cudaError_t set_signs(mck_plan_s* p, const float* B, cudaStream_t s);
 
 // ---- fwht.cu -------------------------------------------------------------
-cudaError_t launch_fwht(float* x, int64_t n, int L, int num_sms, cudaStream_t s);
+// regime: one of mck_fwht_regime_t (only d = 2^16, 2^17 have a choice).
+cudaError_t launch_fwht(float* x, int64_t n, int L, int num_sms, cudaStream_t s,
+                        int regime = MCK_FWHT_AUTO);
 // H over index bits 15..L-1 of n vectors of 2^L (FP32 column pass; 16 <= L <= 20).
 cudaError_t launch_fwht_high_bits(float* x, int64_t n, int L, int num_sms, cudaStream_t s);
 
@@ -82,18 +87,32 @@ struct FeatureArgs {
   const uint32_t* maskA;
   const uint32_t* permS;  // d = 1024: skewed gather tables (see mck_plan_s); null when absent
   const uint32_t* ubase;
+  int32_t rows_per_item;  // launch shape (mck_plan_set_launch): 0 = automatic
+  int32_t staged;         // -1 = automatic
   int32_t E;
   int L;
   int num_sms;
 };
 
 cudaError_t launch_features(const FeatureArgs& a, float* phi, cudaStream_t s);
+// ---- chunks.cu: features at 2^11 <= d <= 2^14 -------------------------------
+cudaError_t launch_chunked_features(const FeatureArgs& a, bool vec_x, float* phi, cudaStream_t s);
 // Partial logits per (sample, expansion): part is n x E x C; then logits = sum_e part + b.
 // At d = 1024 the tile kernel writes logits directly and `part` is unused.
 // Floats of partial logits launch_logits needs in `part` (0: none).
 int64_t logits_scratch_floats(int L, int64_t n, int E, int C, int num_sms);
 cudaError_t launch_logits(const FeatureArgs& a, const float* W, const float* b, int C,
                           float* part, float* logits, cudaStream_t s);
+
+// ---- large.cu: multi-pass forms (features above 2^15, the adjoint above 2^10) --
+// Floats of scratch the multi-pass calls need (C > 0: fused logits).
+int64_t multipass_scratch_floats(int L, int64_t n, int E, int C, bool backward);
+// Features (phi) or, when logits is given, softmax-ready logits W phi + b.
+cudaError_t launch_features_multipass(const FeatureArgs& a, float* phi, const float* W,
+                                      const float* b, int C, float* logits, float* scratch,
+                                      cudaStream_t s);
+struct BackwardArgs;
+cudaError_t launch_backward_multipass(const BackwardArgs& b, float* scratch, cudaStream_t s);
 
 // ---- train.cu ------------------------------------------------------------
 cudaError_t launch_softmax_xent(const float* logits, const int32_t* labels, int64_t n, int C,

@@ -307,6 +307,40 @@ __global__ void k_plan_chunk_tables(const uint32_t* __restrict__ perm, const flo
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Durstenfeld's Fisher-Yates on the host for d > 2^15, exactly as
+// k_plan_perm: for i = d-1 .. 1, j = mulhi(w0, i + 1) of Philox counter
+// (i, e, 2, 0), swap L[i] and L[j]. Expansions on host threads; the result is
+// copied to p->perm on stream s (and waited for).
+mck_status_t host_perm(mck_plan_s* p, cudaStream_t s) {
+  const int64_t d = p->d, E = p->E;
+  const uint32_t k0 = (uint32_t)(p->seed & 0xffffffffu), k1 = (uint32_t)(p->seed >> 32);
+  std::vector<uint32_t> perm((size_t)(d * E));
+  auto shuffle = [&](int64_t e) {
+    uint32_t* L = perm.data() + e * d;
+    for (int64_t i = 0; i < d; ++i) L[i] = (uint32_t)i;
+    for (int64_t i = d - 1; i >= 1; --i) {
+      const U32x4 w = philox4x32_10((uint32_t)i, (uint32_t)e, kTagPerm, 0, k0, k1);
+      const uint32_t j = mulhi_u32(w.x, (uint32_t)(i + 1));
+      const uint32_t a = L[i];
+      L[i] = L[j];
+      L[j] = a;
+    }
+  };
+  const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(E, std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (int64_t t = 1; t < nt; ++t)
+    pool.emplace_back([&, t] {
+      for (int64_t e = t; e < E; e += nt) shuffle(e);
+    });
+  for (int64_t e = 0; e < E; e += nt) shuffle(e);
+  for (auto& th : pool) th.join();
+  cudaError_t err = cudaMemcpyAsync(p->perm, perm.data(), sizeof(uint32_t) * perm.size(),
+                                    cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return cuda_fail(err, "plan: permutation upload");
+  return MCK_OK;
+}
+
 template <int L>
 void launch_chunk_tables(mck_plan_s* p, cudaStream_t s) {
   k_plan_chunk_tables<L><<<blocks_for(p->d * p->E, 256), 256, 0, s>>>(p->perm, p->G, p->B_bits,
@@ -393,12 +427,23 @@ mck_status_t build_tables(mck_plan_s* p, cudaStream_t s) {
     else
       k_plan_matern<false><<<(unsigned)(d * E), threads, 0, s>>>(p->Cs, norm, d, p->matern_t, inv, k0, k1);
   }
-  const size_t perm_smem = sizeof(uint32_t) * (size_t)(d + 1024);
-  err = cudaFuncSetAttribute(k_plan_perm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)perm_smem);
-  if (err == cudaSuccess) {
-    k_plan_perm<<<(unsigned)E, 1024, perm_smem, s>>>(p->perm, d, k0, k1);
-    err = cudaGetLastError();
+  if (d <= ((int64_t)1 << 15)) {
+    const size_t perm_smem = sizeof(uint32_t) * (size_t)(d + 1024);
+    err = cudaFuncSetAttribute(k_plan_perm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)perm_smem);
+    if (err == cudaSuccess) {
+      k_plan_perm<<<(unsigned)E, 1024, perm_smem, s>>>(p->perm, d, k0, k1);
+      err = cudaGetLastError();
+    }
+  } else {
+    // The list no longer fits in shared memory: the same shuffle on the host
+    // (the same Philox draws and swaps, so the same permutation).
+    const mck_status_t st = host_perm(p, s);
+    if (st != MCK_OK) {
+      cudaFreeAsync(G64, s);
+      cudaFreeAsync(norm, s);
+      return st;
+    }
   }
   if (err == cudaSuccess) err = launch_layout_tables(p, s);
   cudaFreeAsync(G64, s);

@@ -52,7 +52,7 @@ def _plan(lib, d=1024, E=1, kernel=0, sigma=1.0, t=40, seed=1, device=-1, out=Tr
 
 @pytest.mark.parametrize("kw,status", [
     (dict(d=3), -1), (dict(d=0), -1), (dict(d=1), -1), (dict(d=-8), -1),
-    (dict(d=1 << 16), -5), (dict(E=0), -1), (dict(E=70000), -1), (dict(kernel=3), -1), (dict(kernel=-1), -1),
+    (dict(d=1 << 21), -5), (dict(d=1 << 16, kernel=1), -5), (dict(E=0), -1), (dict(E=70000), -1), (dict(kernel=3), -1), (dict(kernel=-1), -1),
     (dict(sigma=0.0), -1), (dict(sigma=-1.0), -1), (dict(sigma=float("inf")), -1),
     (dict(sigma=float("nan")), -1), (dict(kernel=1, t=0), -1), (dict(device=-2), -1),
     (dict(out=False), -1), (dict(d=1 << 15, E=1 << 14), -1),

@@ -45,12 +45,14 @@ def test_binding_errors(mck, dev):
         mck.features(plan, torch.zeros((3, 2000), device=dev))  # in_dim > d
     with pytest.raises(TypeError):
         mck.features(plan, torch.zeros((3, 784), device=dev, dtype=torch.float64))
-    with pytest.raises(mck.MckError):
-        mck.Plan(1 << 16, 1)
+    with pytest.raises(mck.MckError, match="UNSUPPORTED"):
+        mck.Plan(1 << 21, 1)
+    with pytest.raises(mck.MckError, match="UNSUPPORTED"):
+        mck.Plan(1 << 16, 1, "matern")
     with pytest.raises(mck.MckError):
         mck.fused_logits(plan, torch.zeros((2, 784), device=dev),
                          torch.zeros((17, plan.num_features), device=dev))
-    big = mck.Plan(4096, 1, "rbf", 1.0, 1)
+    small = mck.Plan(16, 1, "rbf", 1.0, 1)  # the adjoint needs d >= 32
     with pytest.raises(mck.MckError, match="UNSUPPORTED"):
-        mck.features_backward(big, torch.zeros((2, 784), device=dev),
-                              torch.zeros((2, big.num_features), device=dev))
+        mck.features_backward(small, torch.zeros((2, 16), device=dev),
+                              torch.zeros((2, small.num_features), device=dev))

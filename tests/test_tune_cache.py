@@ -20,3 +20,12 @@ def test_cache_roundtrip(tmp_path):
     p = tmp_path / "ok.json"
     p.write_text(json.dumps({"k": {"grain": 8, "ms": {"8": 1.0}}}))
     assert tune._read_cache(str(p))["k"]["grain"] == 8
+
+
+def test_feature_and_grain_entries_share_one_file(tmp_path):
+    p = str(tmp_path / "c.json")
+    tune._write_cache(p, "a", {"grain": 4, "ms": {"4": 1.0}})
+    tune._write_cache(p, "b", {"kind": "features", "rows_per_item": 2, "staged": 1,
+                               "ms": {"2,1": 0.5}})
+    data = tune._read_cache(p)
+    assert data["a"]["grain"] == 4 and data["b"]["rows_per_item"] == 2
