@@ -193,6 +193,41 @@ mck_status_t mck_features(mck_plan_t plan, const float* x, int64_t n, int64_t in
                           int64_t ldx, const float* Cs, const float* G, float* phi,
                           mck_stream_t stream);
 
+/* ---- Host buffers ------------------------------------------------------------
+ * Features of a batch held in HOST memory, written to host memory: the batch
+ * moves in chunks of rows; each chunk's host-to-device copy, feature kernel
+ * and device-to-host copy are queued on one of the pipe's streams, so the
+ * copies of different chunks overlap one another and the kernels. A pipe owns
+ * its streams and per-stream device buffers (chunk_rows x in_dim inputs,
+ * chunk_rows x 2Ed features, and the multi-pass scratch above d = 2^15), made
+ * once: calls allocate nothing. */
+typedef struct mck_host_pipe_s* mck_host_pipe_t;
+#define MCK_HOST_PIPE_MAX_STREAMS 16
+
+/* Make a pipe for `plan` (which must outlive it) and inputs in_dim wide.
+ *   chunk_rows  rows per chunk (>= 1); streams 1..MCK_HOST_PIPE_MAX_STREAMS.
+ * Errors: MCK_EINVAL, MCK_ENOMEM (device buffers), MCK_ECUDA. */
+mck_status_t mck_host_pipe_create(mck_host_pipe_t* out, mck_plan_t plan, int64_t in_dim,
+                                  int64_t chunk_rows, int32_t streams);
+
+/* phi = features of n samples, host to host, through the pipe.
+ *   x     HOST n x in_dim float32 (ld ldx >= in_dim); pinned memory
+ *         (cudaHostAlloc / cudaHostRegister) lets the copies run asynchronously
+ *         and overlap the kernels; pageable memory works, with copies staged by
+ *         the driver
+ *   Cs, G DEVICE E x d or NULL (plan tables), as in mck_features
+ *   phi   HOST n x 2Ed float32, the layout of mck_features
+ * Stream-ordered: the pipe's streams start after the work queued on `stream`
+ * so far, and `stream` waits for every chunk; synchronise `stream` before
+ * reading phi. Calls on one pipe must not overlap (they share its buffers).
+ * Host arrays are not extent-checked (their size is the caller's); a device
+ * pointer returns MCK_EINVAL. */
+mck_status_t mck_features_host(mck_host_pipe_t pipe, const float* x, int64_t n, int64_t ldx,
+                               const float* Cs, const float* G, float* phi, mck_stream_t stream);
+
+/* Release a pipe (synchronises its streams first). NULL is ignored. */
+void mck_host_pipe_destroy(mck_host_pipe_t pipe);
+
 /* Gradients of sum(phi(x) * dphi) (the adjoint of mck_features, with H^T = H
  * and Pi^T = Pi^{-1}; the forward is recomputed, nothing is stored).
  * 32 <= d <= 2^20: fused kernels up to d = 1024, passes over stream-ordered

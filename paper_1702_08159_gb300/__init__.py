@@ -214,41 +214,43 @@ def features(plan, x, Cs=None, G=None, out=None):
 
 
 class HostPipeline:
-    """Streams and device buffers for ``features_host``, made once and reused:
-    `streams` CUDA streams, each with a chunk of `chunk_rows` input rows
-    (in_dim wide) and of their features on the plan's device. Each stream
-    only ever reuses its own buffers, after its previous chunk, so calls need
-    no allocation and no extra synchronisation."""
+    """A host-buffer pipeline of the C ABI (mck_host_pipe_create): `streams`
+    CUDA streams, each with device buffers for a chunk of `chunk_rows` input
+    rows (in_dim wide) and of their features, made once and reused, so calls
+    allocate nothing. Each chunk's host-to-device copy, feature kernel and
+    device-to-host copy run on one stream (mck_features_host)."""
 
     def __init__(self, plan, in_dim, chunk_rows=2048, streams=4):
-        dev = torch.device("cuda", plan.device)
         self.plan, self.in_dim = plan, int(in_dim)
         self.rows = max(1, int(chunk_rows))
-        self.streams = [torch.cuda.Stream(device=dev) for _ in range(max(1, int(streams)))]
-        self.bufs = [(torch.empty((self.rows, self.in_dim), device=dev, dtype=torch.float32),
-                      torch.empty((self.rows, plan.num_features), device=dev, dtype=torch.float32))
-                     for _ in self.streams]
+        self.handle = None
+        h = ctypes.c_void_p()
+        with torch.cuda.device(plan.device):
+            check(load().mck_host_pipe_create(ctypes.byref(h), plan.handle, self.in_dim, self.rows,
+                                              int(streams)), "mck_host_pipe_create")
+        self.handle = h
 
     def run(self, x, out, Cs=None, G=None):
         """Features of the host batch x into the host array out; stream-ordered
         (the current stream waits for every chunk)."""
-        plan = self.plan
+        Cs, G = _tables(self.plan, Cs, G)
         n = x.shape[0]
-        main = torch.cuda.current_stream(torch.device("cuda", plan.device))
-        k = min(len(self.streams), (n + self.rows - 1) // self.rows)
-        for s in self.streams[:k]:
-            s.wait_stream(main)  # inputs, tables and the previous call's readers
-        for i, a in enumerate(range(0, n, self.rows)):
-            b = min(a + self.rows, n)
-            s = self.streams[i % k]
-            xb, pb = self.bufs[i % k]
-            with torch.cuda.stream(s):
-                xb[: b - a].copy_(x[a:b], non_blocking=True)
-                features(plan, xb[: b - a], Cs, G, out=pb[: b - a])
-                out[a:b].copy_(pb[: b - a], non_blocking=True)
-        for s in self.streams[:k]:
-            main.wait_stream(s)
+        dev = torch.device("cuda", self.plan.device)
+        with torch.cuda.device(dev):
+            check(load().mck_features_host(self.handle, _ptr(x), n, self.in_dim, _ptr(Cs), _ptr(G),
+                                           _ptr(out), _stream(dev)), "mck_features_host")
         return out
+
+    def close(self):
+        if self.handle is not None:
+            load().mck_host_pipe_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def features_host(plan, x, out=None, Cs=None, G=None, chunk_rows=2048, streams=4,

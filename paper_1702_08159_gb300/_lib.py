@@ -52,6 +52,9 @@ SIGNATURES = {
     "mck_fwht": (_ST, [_P, _I64, _I64, _I32, _P]),
     "mck_fwht_ex": (_ST, [_P, _I64, _I64, _I32, _I32, _P]),
     "mck_plan_set_launch": (_ST, [_P, _I32, _I32]),
+    "mck_host_pipe_create": (_ST, [ctypes.POINTER(_P), _P, _I64, _I64, _I32]),
+    "mck_features_host": (_ST, [_P, _P, _I64, _I64, _P, _P, _P, _P]),
+    "mck_host_pipe_destroy": (None, [_P]),
     "mck_plan_get_launch": (_ST, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "mck_features": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P]),
     "mck_features_backward": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, _P]),

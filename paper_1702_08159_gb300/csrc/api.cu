@@ -661,3 +661,128 @@ extern "C" mck_status_t mck_fused_logits_noalloc(mck_plan_t p, const float* x, i
                                 logits, (cudaStream_t)stream),
                   "mck_fused_logits_noalloc");
 }
+
+// ---------------------------------------------------------------------------
+// Host-buffer features: chunks of rows through per-stream device buffers.
+// ---------------------------------------------------------------------------
+struct mck_host_pipe_s {
+  mck_plan_s* plan = nullptr;
+  int64_t in_dim = 0, rows = 0, scratch_floats = 0;
+  int ns = 0;
+  cudaStream_t st[MCK_HOST_PIPE_MAX_STREAMS] = {};
+  cudaEvent_t done[MCK_HOST_PIPE_MAX_STREAMS] = {};
+  cudaEvent_t start = nullptr;
+  float* xd[MCK_HOST_PIPE_MAX_STREAMS] = {};
+  float* pd[MCK_HOST_PIPE_MAX_STREAMS] = {};
+  float* sc[MCK_HOST_PIPE_MAX_STREAMS] = {};
+};
+
+extern "C" void mck_host_pipe_destroy(mck_host_pipe_t h) {
+  if (!h) return;
+  {
+    DeviceScope scope(h->plan->device);
+    for (int i = 0; i < h->ns; ++i) {
+      if (h->st[i]) cudaStreamSynchronize(h->st[i]);
+      cudaFree(h->xd[i]);
+      cudaFree(h->pd[i]);
+      cudaFree(h->sc[i]);
+      if (h->done[i]) cudaEventDestroy(h->done[i]);
+      if (h->st[i]) cudaStreamDestroy(h->st[i]);
+    }
+    if (h->start) cudaEventDestroy(h->start);
+    cudaGetLastError();
+  }
+  delete h;
+}
+
+extern "C" mck_status_t mck_host_pipe_create(mck_host_pipe_t* out, mck_plan_t p, int64_t in_dim,
+                                             int64_t chunk_rows, int32_t streams) {
+  if (!out) return fail(MCK_EINVAL, "out is NULL");
+  MCK_TRY(check_plan(p));
+  if (in_dim < 1 || in_dim > p->d) return fail(MCK_EINVAL, "in_dim must be in [1, d]");
+  if (chunk_rows < 1) return fail(MCK_EINVAL, "chunk_rows must be >= 1");
+  if (streams < 1 || streams > MCK_HOST_PIPE_MAX_STREAMS)
+    return fail(MCK_EINVAL, "streams must be in [1, MCK_HOST_PIPE_MAX_STREAMS]");
+  DeviceScope scope(p->device);
+  if (!scope.ok) return fail(MCK_ECUDA, "cannot select the plan's device");
+  mck_host_pipe_s* h = new (std::nothrow) mck_host_pipe_s();
+  if (!h) return fail(MCK_ENOMEM, "pipe allocation failed");
+  h->plan = p;
+  h->in_dim = in_dim;
+  h->rows = chunk_rows;
+  h->ns = streams;
+  const int64_t F = 2 * p->E * p->d;
+  h->scratch_floats = p->L > 15 ? multipass_scratch_floats(p->L, chunk_rows, p->E, 0, false) : 0;
+  bool ok = cudaEventCreateWithFlags(&h->start, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; ok && i < streams; ++i) {
+    ok = cudaStreamCreateWithFlags(&h->st[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&h->done[i], cudaEventDisableTiming) == cudaSuccess &&
+         cudaMalloc(&h->xd[i], sizeof(float) * (size_t)(chunk_rows * in_dim)) == cudaSuccess &&
+         cudaMalloc(&h->pd[i], sizeof(float) * (size_t)(chunk_rows * F)) == cudaSuccess &&
+         (h->scratch_floats == 0 ||
+          cudaMalloc(&h->sc[i], sizeof(float) * (size_t)h->scratch_floats) == cudaSuccess);
+  }
+  if (!ok) {
+    cudaGetLastError();
+    mck_host_pipe_destroy(h);
+    return fail(MCK_ENOMEM, "pipe streams or device buffers could not be made");
+  }
+  *out = h;
+  return MCK_OK;
+}
+
+// Host memory (pinned or pageable), not device or managed memory.
+static mck_status_t check_host(const void* ptr, const char* name) {
+  if (!ptr) return fail(MCK_EINVAL, std::string(name) + " is NULL");
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return MCK_OK;  // not known to CUDA: pageable host memory
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)
+    return fail(MCK_EINVAL, std::string(name) + " is device memory; mck_features takes device arrays");
+  return MCK_OK;
+}
+
+extern "C" mck_status_t mck_features_host(mck_host_pipe_t h, const float* x, int64_t n, int64_t ldx,
+                                          const float* Cs, const float* G, float* phi,
+                                          mck_stream_t stream) {
+  if (!h) return fail(MCK_EINVAL, "pipe is NULL");
+  mck_plan_s* p = h->plan;
+  if (n < 0) return fail(MCK_EINVAL, "n < 0");
+  if (ldx < h->in_dim) return fail(MCK_EINVAL, "ldx < in_dim");
+  if (n == 0) return MCK_OK;
+  DeviceScope scope(p->device);
+  if (!scope.ok) return fail(MCK_ECUDA, "cannot select the plan's device");
+  MCK_TRY(check_host(x, "x"));
+  MCK_TRY(check_host(phi, "phi"));
+  MCK_TRY(check_tables(p, Cs, G));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t F = 2 * p->E * p->d;
+  const int64_t chunks = (n + h->rows - 1) / h->rows;
+  const int k = (int)std::min<int64_t>(h->ns, chunks);
+  cudaError_t err = cudaEventRecord(h->start, s);
+  for (int i = 0; err == cudaSuccess && i < k; ++i) err = cudaStreamWaitEvent(h->st[i], h->start, 0);
+  for (int64_t c = 0; err == cudaSuccess && c < chunks; ++c) {
+    const int i = (int)(c % k);
+    const int64_t a = c * h->rows, rows = std::min<int64_t>(h->rows, n - a);
+    cudaStream_t si = h->st[i];
+    err = ldx == h->in_dim
+              ? cudaMemcpyAsync(h->xd[i], x + a * ldx, sizeof(float) * rows * ldx,
+                                cudaMemcpyHostToDevice, si)
+              : cudaMemcpy2DAsync(h->xd[i], sizeof(float) * h->in_dim, x + a * ldx,
+                                  sizeof(float) * ldx, sizeof(float) * h->in_dim, rows,
+                                  cudaMemcpyHostToDevice, si);
+    if (err != cudaSuccess) break;
+    const FeatureArgs fa = feature_args(p, h->xd[i], rows, h->in_dim, h->in_dim, Cs, G);
+    err = p->L > 15 ? launch_features_multipass(fa, h->pd[i], nullptr, nullptr, 0, nullptr, h->sc[i], si)
+                    : launch_features(fa, h->pd[i], si);
+    if (err != cudaSuccess) break;
+    err = cudaMemcpyAsync(phi + a * F, h->pd[i], sizeof(float) * rows * F, cudaMemcpyDeviceToHost, si);
+  }
+  for (int i = 0; err == cudaSuccess && i < k; ++i) {
+    err = cudaEventRecord(h->done[i], h->st[i]);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(s, h->done[i], 0);
+  }
+  return launched(err, "mck_features_host");
+}

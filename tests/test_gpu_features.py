@@ -158,6 +158,26 @@ def test_laplace(mck, dev, d, E, n):
     plan.close()
 
 
+def test_features_host_pageable_and_large_d(mck, dev):
+    """mck_features_host with pageable (not pinned) host arrays, and at
+    d = 2^16 where each chunk runs the multi-pass form: equal to the device
+    call; a device array is refused."""
+    for d, E, n, chunk in ((1024, 2, 45, 16), (1 << 16, 1, 5, 2)):
+        plan = mck.Plan(d, E, "rbf", 3.0, 8)
+        x = torch.from_numpy(wl.mnist_like(n, 784, seed=n))  # pageable
+        out = torch.full((n, plan.num_features), float("nan"))
+        mck.features_host(plan, x, out=out, chunk_rows=chunk, streams=3)
+        torch.cuda.synchronize()
+        assert torch.equal(out, mck.features(plan, x.to(dev)).cpu())
+        plan.close()
+    plan = mck.Plan(256, 1, "rbf", 1.0, 1)
+    pipe = mck.HostPipeline(plan, 200, 8, 2)
+    with pytest.raises(mck.MckError, match="device memory"):
+        pipe.run(torch.zeros((4, 200), device=dev), torch.zeros((4, plan.num_features)))
+    pipe.close()
+    plan.close()
+
+
 @pytest.mark.parametrize("n,chunk,streams", [(1000, 128, 3), (37, 64, 4), (300, 300, 2)])
 def test_features_host_pipeline(mck, dev, n, chunk, streams):
     """Host-buffer path: chunks over several streams, copies overlapping the
