@@ -434,7 +434,7 @@ def main():
         if "e2e" in legs:
             line["e2e"] = e2e_leg(mck, plan, x_host, dev, stream, world)
         if "logits" in legs:
-            line["fused_logits"] = fused_logits_leg(mck, plan, x, dev, stream, args)
+            line["fused_logits"] = fused_logits_leg(mck, plan, x, dev, stream, args, phi)
         if "train" in legs:
             line["train_step"] = train_step_leg(mck, dev, stream, args)
         if "sweep" in legs:
@@ -514,7 +514,11 @@ def e2e_leg(mck, plan, x_host, dev, stream, world):
             "chunk_rows": E2E_CHUNK_ROWS, "streams": E2E_STREAMS}
 
 
-def fused_logits_leg(mck, plan, x, dev, stream, args):
+def fused_logits_leg(mck, plan, x, dev, stream, args, phi):
+    """Logits W phi + b of the headline batch without writing phi, against
+    the unfused path on the same data: mck_features into the headline's
+    feature buffer, then torch's FP32 addmm (TF32 off, the library's
+    precision)."""
     import torch
 
     import workloads as wl
@@ -523,17 +527,35 @@ def fused_logits_leg(mck, plan, x, dev, stream, args):
     Wd, bd = torch.from_numpy(W).to(dev), torch.from_numpy(b).to(dev)
     n = x.shape[0]
     out = torch.empty((n, C), device=dev)
-    for _ in range(2):
-        mck.fused_logits(plan, x, Wd, bd, out=out)
-    torch.cuda.synchronize()
     steps = max(3, args.steps // 4)
-    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(steps):
-        mck.fused_logits(plan, x, Wd, bd, out=out)
-    e.record(stream)
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(e) / steps
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        e.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(e) / steps
+
+    ms = timed(lambda: mck.fused_logits(plan, x, Wd, bd, out=out))
+    tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        unfused = torch.empty_like(out)
+
+        def plain():
+            mck.features(plan, x, out=phi)
+            torch.addmm(bd, phi, Wd.T, out=unfused)
+
+        ms_unfused = timed(plain)
+        ms_gemm = timed(lambda: torch.addmm(bd, phi, Wd.T, out=unfused))
+        diff = float((unfused - out).abs().max())
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = tf32
     # Algorithmic FP32 operations per row: the contraction (2 C 2Ed), the two
     # transforms (2 E d log2 d add/sub) and the G and Cs products (2 E d);
     # sin/cos not counted. Peak: SMs x 128 FP32 lanes x 2 (FMA) x SM clock.
@@ -542,6 +564,9 @@ def fused_logits_leg(mck, plan, x, dev, stream, args):
     peak_t = fp32_peak_tflops(dev)
     return {"rows": n, "samples_per_s": n / (ms / 1e3), "features_per_s": n * F / (ms / 1e3),
             "ms_per_call": ms, "num_classes": C, "gpu_launches_per_call": 1,
+            "unfused": {"ms_per_call": ms_unfused, "ms_gemm_only": ms_gemm,
+                        "path": "mck_features + torch FP32 addmm (TF32 off)",
+                        "speedup_fused": ms_unfused / ms, "max_abs_diff_vs_fused": diff},
             "alu": {"ops_per_row": ops, "achieved_tflops": tflops, "peak_tflops": peak_t,
                     "frac": tflops / peak_t, "bound": "alu (FP32)"}}
 
