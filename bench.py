@@ -70,7 +70,7 @@ def parse():
     p.add_argument("--batch", type=int, default=N,
                    help="rows per GPU (default 60000; smaller values are for profiling captures)")
     p.add_argument("--legs", default="all",
-                   help="comma list of extra legs to run (e2e,logits,train,sweep,uneven,configs01,fsweep) or 'all'")
+                   help="comma list of extra legs to run (e2e,logits,tc,train,sweep,uneven,configs01,fsweep) or 'all'")
     p.add_argument("--uneven-count", type=int, default=10000,
                    help="vectors in the config-4 leg (smaller values are for profiling captures)")
     return p.parse_args()
@@ -425,7 +425,7 @@ def main():
 
     if not args.no_extras:
         legs = set(args.legs.split(",")) if args.legs != "all" else {
-            "e2e", "logits", "train", "sweep", "uneven", "configs01", "fsweep"}
+            "e2e", "logits", "tc", "train", "sweep", "uneven", "configs01", "fsweep"}
         if world > 1 and args.legs == "all":
             # Under torchrun every rank would repeat the single-GPU
             # characterisation legs; with N GPUs only the end-to-end number
@@ -435,6 +435,9 @@ def main():
             line["e2e"] = e2e_leg(mck, plan, x_host, dev, stream, world)
         if "logits" in legs:
             line["fused_logits"] = fused_logits_leg(mck, plan, x, dev, stream, args, phi)
+        if "tc" in legs:
+            line["features_tensor_core"] = tensor_core_features_leg(mck, plan, x, dev, stream, args,
+                                                                    phi)
         if "train" in legs:
             line["train_step"] = train_step_leg(mck, dev, stream, args)
         if "sweep" in legs:
@@ -569,6 +572,45 @@ def fused_logits_leg(mck, plan, x, dev, stream, args, phi):
                         "speedup_fused": ms_unfused / ms, "max_abs_diff_vs_fused": diff},
             "alu": {"ops_per_row": ops, "achieved_tflops": tflops, "peak_tflops": peak_t,
                     "frac": tflops / peak_t, "bound": "alu (FP32)"}}
+
+
+def tensor_core_features_leg(mck, plan, x, dev, stream, args, phi):
+    """The headline batch through mck_features_ex with both transforms on the
+    tensor cores (16-bit operands, FP32 accumulation, with and without the
+    hi/lo split), against the FP32 butterfly kernel on the same batch. The
+    accuracy against the FP64 oracle is held by tests/test_gpu_features_mma.py
+    (fp16 hi/lo: the FP32 bar, 1e-5); here the largest difference from the
+    FP32 kernel's features is reported beside the time."""
+    import torch
+
+    n = x.shape[0]
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        reps = max(5, args.steps // 5)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        e.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(e) / reps
+
+    peak, _ = measured_peaks()
+    bytes_ = n * (IN_DIM * 4 + F * 4)
+    ms32 = timed(lambda: mck.features(plan, x, out=phi))
+    ref = phi[:: max(1, n // 64)].clone()
+    out = {"rows": n, "fp32_butterflies": {"ms": ms32, "gbs": bytes_ / (ms32 / 1e3) / 1e9,
+                                           "frac_of_measured_hbm": bytes_ / (ms32 / 1e3) / 1e9 / peak}}
+    for prec in ("fp16_split", "bf16_split", "fp16", "bf16"):
+        ms = timed(lambda: mck.features(plan, x, out=phi, prec=prec))
+        diff = float((phi[:: max(1, n // 64)] - ref).abs().max())
+        out[prec] = {"ms": ms, "gbs": bytes_ / (ms / 1e3) / 1e9,
+                     "frac_of_measured_hbm": bytes_ / (ms / 1e3) / 1e9 / peak,
+                     "speed_vs_fp32": ms32 / ms, "max_abs_diff_vs_fp32_sampled_rows": diff}
+    return out
 
 
 def fwht_sweep_leg(mck, dev, stream, args):

@@ -228,6 +228,22 @@ mck_status_t mck_features_host(mck_host_pipe_t pipe, const float* x, int64_t n, 
 /* Release a pipe (synchronises its streams first). NULL is ignored. */
 void mck_host_pipe_destroy(mck_host_pipe_t pipe);
 
+/* mck_features with the two transforms in a chosen precision (north-star
+ * form (1) inside the feature map; d = 1024 only, else MCK_EUNSUPPORTED):
+ *   prec  MCK_FP32: mck_features itself. MCK_BF16 / MCK_FP16 / *_SPLIT: each H
+ *         as the Kronecker factorisation H_4 (x) H_16 (x) H_16 with the two H16
+ *         digits on the tensor cores (16-bit data operand, +-1 exact, FP32
+ *         accumulation; *_SPLIT multiplies the hi and lo halves of the data)
+ *         and the last two index bits as FP32 butterflies, in registers; the
+ *         data is scaled per row by a power of two to keep it in fp16's range.
+ *         Only the Pi gather goes through shared memory.
+ * Accuracy against the FP64 oracle is stated in the tests (MCK_FP16_SPLIT
+ * meets the FP32 bar of 1e-5 at the MNIST-shaped workloads; the unsplit forms
+ * do not). Other arguments and errors as mck_features. */
+mck_status_t mck_features_ex(mck_plan_t plan, const float* x, int64_t n, int64_t in_dim,
+                             int64_t ldx, const float* Cs, const float* G, float* phi,
+                             int32_t prec, mck_stream_t stream);
+
 /* Gradients of sum(phi(x) * dphi) (the adjoint of mck_features, with H^T = H
  * and Pi^T = Pi^{-1}; the forward is recomputed, nothing is stored).
  * 32 <= d <= 2^20: fused kernels up to d = 1024, passes over stream-ordered

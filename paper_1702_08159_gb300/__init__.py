@@ -197,8 +197,11 @@ def fwht_(x, prec="fp32", regime="auto"):
     return x
 
 
-def features(plan, x, Cs=None, G=None, out=None):
-    """phi(x): (n, 2 E d); row = E blocks of [cos | sin] (Eq. etn:mcfeatures)."""
+def features(plan, x, Cs=None, G=None, out=None, prec="fp32"):
+    """phi(x): (n, 2 E d); row = E blocks of [cos | sin] (Eq. etn:mcfeatures).
+
+    prec: "fp32" (float32 butterflies), or at d = 1024 the tensor-core forms
+    "fp16_split", "bf16_split", "fp16", "bf16" (mck_features_ex)."""
     _f32_cuda(x, "x", plan.device)
     x, n, in_dim, ld = _rows(x)
     Cs, G = _tables(plan, Cs, G)
@@ -208,8 +211,13 @@ def features(plan, x, Cs=None, G=None, out=None):
         _f32_cuda(out, "out", plan.device)
         if tuple(out.shape) != (n, plan.num_features) or not out.is_contiguous():
             raise ValueError("out must be a contiguous (n, 2 E d) tensor")
-    check(load().mck_features(plan.handle, _ptr(x), n, in_dim, ld, _ptr(Cs), _ptr(G), _ptr(out),
-                              _stream(x.device)), "mck_features")
+    p = _lib.PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    if p == _lib.MCK_FP32:
+        check(load().mck_features(plan.handle, _ptr(x), n, in_dim, ld, _ptr(Cs), _ptr(G),
+                                  _ptr(out), _stream(x.device)), "mck_features")
+    else:
+        check(load().mck_features_ex(plan.handle, _ptr(x), n, in_dim, ld, _ptr(Cs), _ptr(G),
+                                     _ptr(out), p, _stream(x.device)), "mck_features_ex")
     return out
 
 

@@ -57,6 +57,7 @@ SIGNATURES = {
     "mck_host_pipe_destroy": (None, [_P]),
     "mck_plan_get_launch": (_ST, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "mck_features": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P]),
+    "mck_features_ex": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _I32, _P]),
     "mck_features_backward": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, _P]),
     "mck_features_backward_ex": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, _P,
                                        _P]),

@@ -27,8 +27,8 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE
 # (no fused multiply-add contraction) so its tables round like a plain IEEE
 # float64 evaluation.
 EXTRA = {"plan.cu": ["--fmad=false"]}
-SOURCES = ["api.cu", "plan.cu", "fwht.cu", "fwht_mma.cu", "features.cu", "chunks.cu", "large.cu",
-           "train.cu", "grouped.cu"]
+SOURCES = ["api.cu", "plan.cu", "fwht.cu", "fwht_mma.cu", "features.cu", "features_mma.cu",
+           "chunks.cu", "large.cu", "train.cu", "grouped.cu"]
 
 
 def nvcc():

@@ -148,6 +148,11 @@ FeatureArgs feature_args(const mck_plan_s* p, const float* x, int64_t n, int64_t
   a.maskA = p->maskA;
   a.permS = p->permS;
   a.ubase = p->ubase;
+  a.mmaMask = p->mmaMask;
+  a.mmaG = G ? nullptr : p->mmaG;     // overriding tables are read in natural order
+  a.mmaCs = Cs ? nullptr : p->mmaCs;
+  a.mmaPerm = p->mmaPerm;
+  a.mmaBase = p->mmaBase;
   a.rows_per_item = p->rows_per_item;
   a.staged = p->staged;
   a.E = p->E;
@@ -276,7 +281,12 @@ mck_status_t mck_plan_ex(mck_plan_t* out, int64_t d, int32_t E, int32_t kernel, 
   }
   if (ok && p->L == 10)
     ok = cudaMalloc(&p->permS, sizeof(uint32_t) * n / 2) == cudaSuccess &&
-         cudaMalloc(&p->ubase, sizeof(uint32_t) * 32 * E) == cudaSuccess;
+         cudaMalloc(&p->ubase, sizeof(uint32_t) * 32 * E) == cudaSuccess &&
+         cudaMalloc(&p->mmaMask, sizeof(uint32_t) * 32 * E) == cudaSuccess &&
+         cudaMalloc(&p->mmaG, sizeof(float) * n) == cudaSuccess &&
+         cudaMalloc(&p->mmaCs, sizeof(float) * n) == cudaSuccess &&
+         cudaMalloc(&p->mmaPerm, sizeof(uint32_t) * n / 2) == cudaSuccess &&
+         cudaMalloc(&p->mmaBase, sizeof(uint32_t) * 32 * E) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     mck_plan_destroy(p);
@@ -317,6 +327,11 @@ void mck_plan_destroy(mck_plan_t p) {
     cudaFree(p->maskA);
     cudaFree(p->permS);
     cudaFree(p->ubase);
+    cudaFree(p->mmaMask);
+    cudaFree(p->mmaG);
+    cudaFree(p->mmaCs);
+    cudaFree(p->mmaPerm);
+    cudaFree(p->mmaBase);
     cudaGetLastError();
   }
   delete p;
@@ -427,6 +442,25 @@ mck_status_t mck_features(mck_plan_t p, const float* x, int64_t n, int64_t in_di
   }
   return launched(launch_features(feature_args(p, x, n, in_dim, ldx, Cs, G), phi, s),
                   "mck_features");
+}
+
+mck_status_t mck_features_ex(mck_plan_t p, const float* x, int64_t n, int64_t in_dim, int64_t ldx,
+                             const float* Cs, const float* G, float* phi, int32_t prec,
+                             mck_stream_t stream) {
+  if (prec == MCK_FP32) return mck_features(p, x, n, in_dim, ldx, Cs, G, phi, stream);
+  MCK_TRY(check_plan(p));
+  if (prec < MCK_BF16 || prec > MCK_FP16_SPLIT) return fail(MCK_EUNSUPPORTED, "unknown precision");
+  if (p->L != 10) return fail(MCK_EUNSUPPORTED, "tensor-core features are built for d = 1024");
+  DeviceScope scope(p->device);
+  MCK_TRY(check_x(p, x, n, in_dim, ldx));
+  MCK_TRY(check_tables(p, Cs, G));
+  const int64_t F = 2 * p->E * p->d;
+  if (n == 0) return MCK_OK;
+  MCK_TRY(check_array(phi, 4 * n * F, p->device, "phi"));
+  if ((uintptr_t)phi % 16) return fail(MCK_EINVAL, "phi must be 16-byte aligned");
+  return launched(launch_features_mma(feature_args(p, x, n, in_dim, ldx, Cs, G), phi, prec,
+                                      (cudaStream_t)stream),
+                  "mck_features_ex");
 }
 
 static mck_status_t run_backward(mck_plan_s* p, BackwardArgs b, cudaStream_t s, const char* who) {

@@ -39,6 +39,14 @@ struct mck_plan_s {
   // gather instruction's 32 sources over the 32 banks.
   uint32_t* permS = nullptr;   // E x d/2: gather byte offsets into the skewed slot, two 16-bit per word
   uint32_t* ubase = nullptr;   // E x 32: word base of lane lam's registers in the skewed slot
+  // d = 1024 only, the tensor-core feature kernel's tables (mma_layout.h
+  // orders): B mask, G (input order) and Cs (output order) lane-ordered as
+  // 8 float4 per lane, and the skewed gather tables for its u layout.
+  uint32_t* mmaMask = nullptr;  // E x 32
+  float* mmaG = nullptr;        // E x d
+  float* mmaCs = nullptr;       // E x d
+  uint32_t* mmaPerm = nullptr;  // E x d/2 packed 16-bit byte offsets
+  uint32_t* mmaBase = nullptr;  // E x 32
   // Launch shape of the batched feature kernels (mck_plan_set_launch).
   int32_t rows_per_item = 0;   // 0 = automatic
   int32_t staged = -1;         // -1 = automatic
@@ -87,6 +95,11 @@ struct FeatureArgs {
   const uint32_t* maskA;
   const uint32_t* permS;  // d = 1024: skewed gather tables (see mck_plan_s); null when absent
   const uint32_t* ubase;
+  const uint32_t* mmaMask;  // d = 1024: the tensor-core kernel's tables (see mck_plan_s)
+  const float* mmaG;
+  const float* mmaCs;
+  const uint32_t* mmaPerm;
+  const uint32_t* mmaBase;
   int32_t rows_per_item;  // launch shape (mck_plan_set_launch): 0 = automatic
   int32_t staged;         // -1 = automatic
   int32_t E;
@@ -95,6 +108,9 @@ struct FeatureArgs {
 };
 
 cudaError_t launch_features(const FeatureArgs& a, float* phi, cudaStream_t s);
+// ---- features_mma.cu: d = 1024 features with the transforms on tensor cores --
+// prec: MCK_BF16, MCK_FP16, MCK_BF16_SPLIT or MCK_FP16_SPLIT.
+cudaError_t launch_features_mma(const FeatureArgs& a, float* phi, int prec, cudaStream_t s);
 // ---- chunks.cu: features at 2^11 <= d <= 2^14 -------------------------------
 cudaError_t launch_chunked_features(const FeatureArgs& a, bool vec_x, float* phi, cudaStream_t s);
 // Partial logits per (sample, expansion): part is n x E x C; then logits = sum_e part + b.

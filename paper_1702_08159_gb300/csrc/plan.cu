@@ -19,6 +19,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "mma_layout.h"
 #include "philox.cuh"
 
 namespace mck {
@@ -370,8 +371,38 @@ __global__ void k_plan_set_signs(const float* __restrict__ B, uint32_t* __restri
   bits[t] = m;
 }
 
+// The tensor-core feature kernel's tables at d = 1024 (mma_layout.h orders):
+// entry t = (e, m, lane, q) of an expansion's 1024 holds G at the input-order
+// element of register j = 4m + q of `lane` and Cs at its output-order element;
+// the mask word (e, lane) has bit j where B_e is -1 at the input-order element.
+__global__ void k_plan_mma_tables(const float* __restrict__ G, const float* __restrict__ Cs,
+                                  const uint32_t* __restrict__ bits, float* __restrict__ mG,
+                                  float* __restrict__ mCs, uint32_t* __restrict__ mMask, int32_t E) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)E * 1024) return;
+  const int64_t e = t / 1024;
+  const int rr = (int)(t % 1024);
+  const int q = rr & 3, lane = (rr >> 2) & 31, m = rr >> 7, j = 4 * m + q;
+  mG[t] = G[e * 1024 + mma_in(lane, j)];
+  mCs[t] = Cs[e * 1024 + mma_out(lane, j)];
+  if (m == 0 && q == 0) {
+    uint32_t mask = 0;
+    for (int jj = 0; jj < 32; ++jj) {
+      const int k = mma_in(lane, jj);
+      mask |= ((bits[e * 32 + (k >> 5)] >> (k & 31)) & 1u) << jj;
+    }
+    mMask[e * 32 + lane] = mask;
+  }
+}
+
 // The lane-ordered copies of Pi, G and the B mask (warp and chunked kernels).
 cudaError_t launch_layout_tables(mck_plan_s* p, cudaStream_t s) {
+  if (p->mmaG) {
+    k_plan_mma_tables<<<blocks_for(p->E * 1024, 256), 256, 0, s>>>(p->G, p->Cs, p->B_bits, p->mmaG,
+                                                                   p->mmaCs, p->mmaMask, p->E);
+    const cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
   if (!p->permB) return cudaSuccess;
   switch (p->L) {
     case 5: launch_lane_tables<5>(p, s); break;
@@ -492,16 +523,20 @@ inline int lane_of(int s) { return (s & 3) | ((s >> 7) << 2); }
 inline int reg_of(int s) { return (s >> 2) & 31; }
 
 // Bases (a permutation of 0..31) for one expansion's permutation pi (1024
-// entries); returns the gather's wavefront count with them.
-int skew_bases(const uint32_t* pi, uint64_t seed, int iters, uint8_t* base) {
+// entries); returns the gather's wavefront count with them. Load j of lane l
+// fills element dest(l, j) of the gather's layout; u element s sits in lane
+// src_lane(s), register src_reg(s) of the stored layout.
+template <class Dest, class SrcLane, class SrcReg>
+int skew_bases(const uint32_t* pi, uint64_t seed, int iters, uint8_t* base, Dest dest,
+               SrcLane src_lane, SrcReg src_reg) {
   // The 32 sources read from each lane group a: (load j, register of source).
   int occ_j[32][32], occ_r[32][32], nocc[32] = {0};
   for (int l = 0; l < 32; ++l)
     for (int j = 0; j < 32; ++j) {
-      const int src = (int)pi[Lay<10>::kB(l, j)];
-      const int a = lane_of(src);
+      const int src = (int)pi[dest(l, j)];
+      const int a = src_lane(src);
       occ_j[a][nocc[a]] = j;
-      occ_r[a][nocc[a]] = reg_of(src);
+      occ_r[a][nocc[a]] = src_reg(src);
       ++nocc[a];
     }
   int f[32], best_f[32];
@@ -582,12 +617,35 @@ mck_status_t build_skew_tables(mck_plan_s* p) {
   const int d = 1024;
   const int64_t E = p->E;
   std::vector<uint32_t> pi((size_t)E * d), permS((size_t)E * d / 2), ubase((size_t)E * 32);
+  std::vector<uint32_t> mPerm((size_t)E * d / 2), mBase((size_t)E * 32);
   cudaError_t err = cudaMemcpy(pi.data(), p->perm, sizeof(uint32_t) * pi.size(), cudaMemcpyDeviceToHost);
   if (err != cudaSuccess) return cuda_fail(err, "plan: skewed gather tables");
+  auto pack = [](const uint32_t* pe, const uint8_t* base, int lam, int i, auto dest, auto slane,
+                 auto sreg) {
+    uint32_t wv = 0;
+    for (int h = 0; h < 2; ++h) {
+      const int src = (int)pe[dest(lam, 2 * i + h)];
+      wv |= (4u * (uint32_t)(base[slane(src)] + 33 * sreg(src))) << (16 * h);
+    }
+    return wv;
+  };
   auto work = [&](int64_t e) {
+    const uint32_t* pe = pi.data() + e * d;
+    const uint64_t seed = p->seed ^ (0x5851F42D4C957F2Dull * (uint64_t)(e + 1));
+    // the tensor-core kernel: gather into the input order, u stored from the output order
+    uint8_t mb[32];
+    auto min_ = [](int l, int j) { return mma_in(l, j); };
+    auto mlane = [](int src) { return mma_out_lane(src); };
+    auto mreg = [](int src) { return mma_out_reg(src); };
+    skew_bases(pe, seed ^ 0x9E3779B97F4A7C15ull, kSkewIters, mb, min_, mlane, mreg);
+    for (int l = 0; l < 32; ++l) mBase[(size_t)e * 32 + l] = mb[l];
+    for (int lam = 0; lam < 32; ++lam)
+      for (int i = 0; i < 16; ++i)
+        mPerm[(size_t)e * (d / 2) + ((size_t)(i >> 2) * 32 + lam) * 4 + (i & 3)] =
+            pack(pe, mb, lam, i, min_, mlane, mreg);
     uint8_t base[32];
-    skew_bases(pi.data() + e * d, p->seed ^ (0x5851F42D4C957F2Dull * (uint64_t)(e + 1)), kSkewIters,
-               base);
+    skew_bases(pe, seed, kSkewIters, base, [](int l, int j) { return Lay<10>::kB(l, j); },
+               [](int src) { return lane_of(src); }, [](int src) { return reg_of(src); });
     for (int l = 0; l < 32; ++l) ubase[(size_t)e * 32 + l] = base[l];
     // Lane lam's 16 packed words: word i holds the byte offsets of its
     // registers 2i (low half) and 2i + 1 (high half); stored as 4 x uint4
@@ -614,6 +672,10 @@ mck_status_t build_skew_tables(mck_plan_s* p) {
   err = cudaMemcpy(p->permS, permS.data(), sizeof(uint32_t) * permS.size(), cudaMemcpyHostToDevice);
   if (err == cudaSuccess)
     err = cudaMemcpy(p->ubase, ubase.data(), sizeof(uint32_t) * ubase.size(), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess && p->mmaPerm)
+    err = cudaMemcpy(p->mmaPerm, mPerm.data(), sizeof(uint32_t) * mPerm.size(), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess && p->mmaBase)
+    err = cudaMemcpy(p->mmaBase, mBase.data(), sizeof(uint32_t) * mBase.size(), cudaMemcpyHostToDevice);
   if (err != cudaSuccess) return cuda_fail(err, "plan: skewed gather tables");
   return MCK_OK;
 }
