@@ -545,6 +545,10 @@ def fused_logits_leg(mck, plan, x, dev, stream, args, phi):
         return a.elapsed_time(e) / steps
 
     ms = timed(lambda: mck.fused_logits(plan, x, Wd, bd, out=out))
+    out_tc = torch.empty_like(out)
+    ms_tc = timed(lambda: mck.fused_logits(plan, x, Wd, bd, out=out_tc, prec="fp16_split"))
+    diff_tc = float((out_tc - out).abs().max())
+    ms_feat = timed(lambda: mck.features(plan, x, out=phi))
     tf32 = torch.backends.cuda.matmul.allow_tf32
     torch.backends.cuda.matmul.allow_tf32 = False
     try:
@@ -565,11 +569,25 @@ def fused_logits_leg(mck, plan, x, dev, stream, args, phi):
     ops = 2 * C * F + 2 * E * D * int(np.log2(D)) + 2 * E * D
     tflops = n * ops / (ms / 1e3) / 1e12
     peak_t = fp32_peak_tflops(dev)
+    hbm, _ = measured_peaks()
+    # The best any unfused path could do: the feature kernel as measured, then
+    # one read of phi at the measured copy bandwidth (the GEMM's floor).
+    ideal_unfused = ms_feat + n * F * 4 / (hbm * 1e9) * 1e3
     return {"rows": n, "samples_per_s": n / (ms / 1e3), "features_per_s": n * F / (ms / 1e3),
             "ms_per_call": ms, "num_classes": C, "gpu_launches_per_call": 1,
+            "tensor_core_fp16_split": {
+                "ms_per_call": ms_tc, "samples_per_s": n / (ms_tc / 1e3),
+                "speedup_vs_fp32_fused": ms / ms_tc, "max_abs_diff_vs_fp32_fused": diff_tc,
+                "gpu_launches_per_call": 2,
+                "path": "mck_fused_logits_ex(MCK_FP16_SPLIT): FP32 features, W phi on the "
+                        "tensor cores (fp16 hi/lo x3, FP32 accumulation)"},
             "unfused": {"ms_per_call": ms_unfused, "ms_gemm_only": ms_gemm,
                         "path": "mck_features + torch FP32 addmm (TF32 off)",
-                        "speedup_fused": ms_unfused / ms, "max_abs_diff_vs_fused": diff},
+                        "speedup_fused": ms_unfused / ms, "max_abs_diff_vs_fused": diff,
+                        "ms_features_only": ms_feat,
+                        "ms_ideal_unfused": ideal_unfused,
+                        "ideal_unfused": "features as measured + one read of phi at the "
+                                         "measured HBM copy bandwidth"},
             "alu": {"ops_per_row": ops, "achieved_tflops": tflops, "peak_tflops": peak_t,
                     "frac": tflops / peak_t, "bound": "alu (FP32)"}}
 

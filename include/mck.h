@@ -228,8 +228,9 @@ mck_status_t mck_features_host(mck_host_pipe_t pipe, const float* x, int64_t n, 
 /* Release a pipe (synchronises its streams first). NULL is ignored. */
 void mck_host_pipe_destroy(mck_host_pipe_t pipe);
 
-/* mck_features with the two transforms in a chosen precision (north-star
- * form (1) inside the feature map; d = 1024 only, else MCK_EUNSUPPORTED):
+/* mck_features with the two transforms in a chosen precision (the
+ * tensor-core Kronecker-H16 transform of mck_fwht inside the feature map of
+ * Eq. etn:mckernel; d = 1024 only, else MCK_EUNSUPPORTED):
  *   prec  MCK_FP32: mck_features itself. MCK_BF16 / MCK_FP16 / *_SPLIT: each H
  *         as the Kronecker factorisation H_4 (x) H_16 (x) H_16 with the two H16
  *         digits on the tensor cores (16-bit data operand, +-1 exact, FP32
@@ -281,6 +282,28 @@ mck_status_t mck_fused_logits(mck_plan_t plan, const float* x, int64_t n, int64_
                               int64_t ldx, const float* Cs, const float* G, const float* W,
                               const float* b, int32_t num_classes, float* logits,
                               mck_stream_t stream);
+
+/* mck_fused_logits with the contraction W phi in a chosen precision (Sec.
+ * "Empirical Analysis and Experiments": softmax(W phi + b); the tensor-core
+ * split-precision contraction):
+ *   prec  MCK_FP32: mck_fused_logits itself (FP32 FMA contraction, any d).
+ *         MCK_FP16_SPLIT (d = 1024 only, else MCK_EUNSUPPORTED): the
+ *         features are computed in FP32 as in mck_features and contracted on
+ *         the tensor cores: each feature and each weight is written as
+ *         hi + lo in fp16 (the weights of class c first scaled by a power of
+ *         two so that their largest magnitude lies in [2^14, 2^15); exact,
+ *         undone at the end), and hi.hi + hi.lo + lo.hi are accumulated in
+ *         FP32. Each product then carries a relative error below ~2^-21;
+ *         the tests hold the logits to the FP32 path's bar of 1e-4 against
+ *         the FP64 oracle. Other precisions return MCK_EUNSUPPORTED.
+ * Takes stream-ordered scratch for the split weights (E x 64 KiB, x 2 above
+ * 8 classes) and, for batches with fewer 12-row tiles than SMs, n x
+ * (expansion chunks) x num_classes partial logits. Other arguments, results
+ * and errors as mck_fused_logits. */
+mck_status_t mck_fused_logits_ex(mck_plan_t plan, const float* x, int64_t n, int64_t in_dim,
+                                 int64_t ldx, const float* Cs, const float* G, const float* W,
+                                 const float* b, int32_t num_classes, float* logits,
+                                 int32_t prec, mck_stream_t stream);
 
 /* Capacity, in floats, of the fixed scratch used by mck_fused_logits_noalloc. */
 #define MCK_NOALLOC_MAX_PARTIALS (1 << 22) /* 4,194,304 floats = 16 MiB per device */

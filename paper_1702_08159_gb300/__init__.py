@@ -318,8 +318,10 @@ def features_backward(plan, x, dphi, Cs=None, G=None, need_dx=True, need_dCs=Tru
     return (dx, dCs, dG, dB) if need_dB else (dx, dCs, dG)
 
 
-def fused_logits(plan, x, W, b=None, Cs=None, G=None, out=None):
-    """W phi(x) + b without materialising phi: (n, num_classes)."""
+def fused_logits(plan, x, W, b=None, Cs=None, G=None, out=None, prec="fp32"):
+    """W phi(x) + b without materialising phi: (n, num_classes). prec "fp32"
+    contracts with FP32 FMAs (any d); "fp16_split" on the tensor cores (fp16
+    hi/lo split of features and weights, FP32 accumulation; d = 1024)."""
     _f32_cuda(x, "x", plan.device)
     x, n, in_dim, ld = _rows(x)
     Cs, G = _tables(plan, Cs, G)
@@ -331,8 +333,15 @@ def fused_logits(plan, x, W, b=None, Cs=None, G=None, out=None):
         b = _f32_cuda(b, "b", plan.device).contiguous()
     if out is None:
         out = torch.empty((n, C), device=x.device, dtype=torch.float32)
-    check(load().mck_fused_logits(plan.handle, _ptr(x), n, in_dim, ld, _ptr(Cs), _ptr(G), _ptr(W),
-                                  _ptr(b), C, _ptr(out), _stream(x.device)), "mck_fused_logits")
+    if prec == "fp32":
+        check(load().mck_fused_logits(plan.handle, _ptr(x), n, in_dim, ld, _ptr(Cs), _ptr(G),
+                                      _ptr(W), _ptr(b), C, _ptr(out), _stream(x.device)),
+              "mck_fused_logits")
+    else:
+        check(load().mck_fused_logits_ex(plan.handle, _ptr(x), n, in_dim, ld, _ptr(Cs), _ptr(G),
+                                         _ptr(W), _ptr(b), C, _ptr(out),
+                                         _lib.PRECISIONS[prec] if isinstance(prec, str) else int(prec),
+                                         _stream(x.device)), "mck_fused_logits_ex")
     return out
 
 

@@ -62,6 +62,7 @@ SIGNATURES = {
     "mck_features_backward_ex": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, _P,
                                        _P]),
     "mck_fused_logits": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _I32, _P, _P]),
+    "mck_fused_logits_ex": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _I32, _P, _I32, _P]),
     "mck_fused_logits_noalloc": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _I32, _P, _P]),
     "mck_fused_logits_backward": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _I32, _P, _P, _P,
                                         _P, _P, _P, _P]),

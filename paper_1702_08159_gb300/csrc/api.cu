@@ -540,6 +540,33 @@ mck_status_t mck_fused_logits(mck_plan_t p, const float* x, int64_t n, int64_t i
                   "mck_fused_logits");
 }
 
+mck_status_t mck_fused_logits_ex(mck_plan_t p, const float* x, int64_t n, int64_t in_dim,
+                                 int64_t ldx, const float* Cs, const float* G, const float* W,
+                                 const float* b, int32_t C, float* logits, int32_t prec,
+                                 mck_stream_t stream) {
+  if (prec == MCK_FP32) return mck_fused_logits(p, x, n, in_dim, ldx, Cs, G, W, b, C, logits, stream);
+  MCK_TRY(check_plan(p));
+  if (prec != MCK_FP16_SPLIT)
+    return fail(MCK_EUNSUPPORTED, "the tensor-core contraction is built for MCK_FP16_SPLIT");
+  if (p->L != 10) return fail(MCK_EUNSUPPORTED, "the tensor-core contraction is built for d = 1024");
+  if (C < 1 || C > MCK_MAX_CLASSES) return fail(MCK_EINVAL, "num_classes must be in [1, 16]");
+  DeviceScope scope(p->device);
+  MCK_TRY(check_x(p, x, n, in_dim, ldx));
+  MCK_TRY(check_tables(p, Cs, G));
+  const int64_t F = 2 * p->E * p->d;
+  MCK_TRY(check_array(W, 4 * C * F, p->device, "W"));
+  if ((uintptr_t)W % 16) return fail(MCK_EINVAL, "W must be 16-byte aligned");
+  MCK_TRY(check_array(b, 4 * C, p->device, "b", true));
+  if (n == 0) return MCK_OK;
+  MCK_TRY(check_array(logits, 4 * n * C, p->device, "logits"));
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch sc(s);
+  MCK_TRY(sc.alloc(sizeof(float) * (size_t)logits_mma_scratch_floats(n, p->E, C, p->num_sms)));
+  return launched(launch_logits_mma(feature_args(p, x, n, in_dim, ldx, Cs, G), W, b, C,
+                                    (float*)sc.ptr, logits, s),
+                  "mck_fused_logits_ex");
+}
+
 mck_status_t mck_fused_logits_backward_ex(mck_plan_t p, const float* x, int64_t n,
                                           int64_t in_dim, int64_t ldx, const float* Cs,
                                           const float* G, const float* W, int32_t C,

@@ -31,6 +31,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "mma_h16.cuh"
 
 namespace mck {
 namespace {
@@ -51,6 +52,8 @@ struct Launch {
   const float* W;     // MODE_LOGITS: C x 2Ed
   float* part;        // MODE_LOGITS: n x E x C
   int C;
+  const uint4* wf;    // tensor-core logits: fp16 hi/lo fragments of the scaled W
+  const float* winv;  // tensor-core logits: the per-class inverse scales
 };
 
 // Flip the sign of register j where bit j of `mask` is set (B = -1).
@@ -588,6 +591,107 @@ __device__ __forceinline__ void load_w_col(const float* __restrict__ Wg, int64_t
   }
 }
 
+// x = hi + lo + O(2^-22 x) with hi, lo fp16 (pairs packed as half2).
+__device__ __forceinline__ void split_f16(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(a, b);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);  // both differences are exact
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// Word offset, inside a row of the tensor-core logits' feature buffer, of
+// the fp16 (hi, lo) pair words of features f, f + 1 (f even). The 16
+// features of k-step ks take words [16 ks, 16 ks + 16) in four 4-word chunks;
+// chunk (t + rho) & 3, rho = (ks >> 1) & 3, holds (hi, lo) of the pairs at
+// features 16 ks + 2t and 16 ks + 2t + 8: one 16-byte load gives a lane
+// (g, t) of mma.m16n8k16 its A registers a0 / a2 of row g (hi and lo). The
+// rotation rho makes both the producers' 8-byte stores (lanes of a warp over
+// 8 k-steps) and the consumers' 16-byte loads (8 lanes over 2 rows) hit 32
+// distinct banks, with the row stride = 16 (mod 32) words.
+__host__ __device__ __forceinline__ constexpr int mma_feat_word(int f) {
+  return 16 * (f >> 4) + 4 * (((((f & 15) >> 1) & 3) + ((f >> 5) & 3)) & 3) + 2 * ((f & 15) >> 3);
+}
+
+// One row-expansion of a fused-logits producer at d = 1024: the features of
+// sample n under expansion e (zeros for an invalid row) into the row slice
+// buf (also the transform's shared slot), cos then sin: FP32 in natural order
+// (buf[0, 2048)), or with SPLIT16 as fp16 hi/lo pairs at mma_feat_word. The
+// feature kernel's sequence: signs, H over layouts A and B, u into the skewed
+// slot, the Pi gather, G, H, z = Cs h.
+template <bool SPLIT16>
+__device__ __forceinline__ void produce_row_1024(const Launch& P, int64_t n, bool valid, int e,
+                                                 int lane, float* buf) {
+  constexpr int L = 10;
+  using Y = Lay<L>;
+  constexpr int d = Y::d;
+  const uint32_t slot = smem_addr(buf);
+  const int64_t off = (int64_t)e * d;
+  const uint32_t bmask = __ldg(P.a.maskA + (int64_t)e * Y::T + lane);
+  const uint32_t ubase = __ldg(P.a.ubase + (int64_t)e * 32 + lane);
+  uint32_t poff[16];
+  float gt[32];
+  load_skew_offsets(P.a.permS + (int64_t)e * (d / 2), lane, poff);
+  if (P.a.GB) {
+    const float4* gb = reinterpret_cast<const float4*>(P.a.GB + off) + lane;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const float4 v = __ldg(gb + m * Y::T);
+      gt[4 * m] = v.x;
+      gt[4 * m + 1] = v.y;
+      gt[4 * m + 2] = v.z;
+      gt[4 * m + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) gt[j] = __ldg(P.a.G + off + Y::kB(lane, j));
+  }
+  float w[32];
+  load_x_A<L>(P, n, valid, lane, w);
+  apply_signs(w, bmask);
+  hreg<Y::maskA()>(w);
+  store_A<L>(buf, 0, lane, w);
+  __syncwarp();
+  load_B<L>(buf, 0, lane, w);
+  hreg<Y::maskB()>(w);
+  store_skew(buf, ubase, w);
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 32; ++j)
+    w[j] = lds32(slot + ((j & 1) ? (poff[j >> 1] >> 16) : (poff[j >> 1] & 0xffffu)));
+  hreg_scaled<Y::maskB()>(w, gt);
+  __syncwarp();
+  store_B<L>(buf, 0, lane, w);
+  __syncwarp();
+  load_A<L>(buf, 0, lane, w);
+  hreg<Y::maskA()>(w);
+  __syncwarp();  // every lane holds its values: the slice takes the features now
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int k0 = Y::kA(lane, 4 * m);
+    const float4 c4 = __ldg(reinterpret_cast<const float4*>(P.a.Cs + off + k0));
+    const float cs[4] = {c4.x, c4.y, c4.z, c4.w};
+    float c[4], s4[4];
+    cos_sin4(cs, &w[4 * m], c, s4);
+    // an invalid row contributes nothing
+    if (!valid) c[0] = c[1] = c[2] = c[3] = s4[0] = s4[1] = s4[2] = s4[3] = 0.f;
+    if constexpr (SPLIT16) {
+      uint2 v;
+      split_f16(c[0], c[1], v.x, v.y);
+      *reinterpret_cast<uint2*>(buf + mma_feat_word(k0)) = v;
+      split_f16(c[2], c[3], v.x, v.y);
+      *reinterpret_cast<uint2*>(buf + mma_feat_word(k0 + 2)) = v;
+      split_f16(s4[0], s4[1], v.x, v.y);
+      *reinterpret_cast<uint2*>(buf + mma_feat_word(d + k0)) = v;
+      split_f16(s4[2], s4[3], v.x, v.y);
+      *reinterpret_cast<uint2*>(buf + mma_feat_word(d + k0 + 2)) = v;
+    } else {
+      *reinterpret_cast<float4*>(buf + k0) = make_float4(c[0], c[1], c[2], c[3]);
+      *reinterpret_cast<float4*>(buf + d + k0) = make_float4(s4[0], s4[1], s4[2], s4[3]);
+    }
+  }
+}
+
 template <int CPT, int CG>
 __global__ void __launch_bounds__(kTileThreads, 1) k_logits_tile(const Launch P,
                                                                  const float* __restrict__ b,
@@ -623,8 +727,6 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_logits_tile(const Launch P,
         const int bsel = (int)(step & 1);
         if (step >= 2) named_barrier(kBarEmpty + bsel, kTileThreads);
         float* buf = phis + (bsel * kTileRows + warp) * F2;
-        const uint32_t slot = smem_addr(buf);
-        const int64_t off = (int64_t)e * d;
         {  // the next step's tables (permS, G, Cs: 80 lines of 128 B) into L1, 10 per warp
           const int64_t offn = (int64_t)(e + 1 < E ? e + 1 : 0) * d;
           if (lane < 10) {
@@ -637,57 +739,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_logits_tile(const Launch P,
             asm volatile("prefetch.global.L1 [%0];" ::"l"(line));
           }
         }
-        const uint32_t bmask = __ldg(P.a.maskA + (int64_t)e * Y::T + lane);
-        const uint32_t ubase = __ldg(P.a.ubase + (int64_t)e * 32 + lane);
-        uint32_t poff[16];
-        float gt[32];
-        load_skew_offsets(P.a.permS + (int64_t)e * (d / 2), lane, poff);
-        if (P.a.GB) {
-          const float4* gb = reinterpret_cast<const float4*>(P.a.GB + off) + lane;
-#pragma unroll
-          for (int m = 0; m < 8; ++m) {
-            const float4 v = __ldg(gb + m * Y::T);
-            gt[4 * m] = v.x;
-            gt[4 * m + 1] = v.y;
-            gt[4 * m + 2] = v.z;
-            gt[4 * m + 3] = v.w;
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) gt[j] = __ldg(P.a.G + off + Y::kB(lane, j));
-        }
-        float w[32];
-        load_x_A<L>(P, n, valid, lane, w);
-        apply_signs(w, bmask);
-        hreg<Y::maskA()>(w);
-        store_A<L>(buf, 0, lane, w);
-        __syncwarp();
-        load_B<L>(buf, 0, lane, w);
-        hreg<Y::maskB()>(w);
-        store_skew(buf, ubase, w);
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          w[j] = lds32(slot + ((j & 1) ? (poff[j >> 1] >> 16) : (poff[j >> 1] & 0xffffu)));
-        hreg_scaled<Y::maskB()>(w, gt);
-        __syncwarp();
-        store_B<L>(buf, 0, lane, w);
-        __syncwarp();
-        load_A<L>(buf, 0, lane, w);
-        hreg<Y::maskA()>(w);
-        __syncwarp();  // every lane holds its values: the slice takes the features now
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const int k0 = Y::kA(lane, 4 * m);
-          const float4 c4 = __ldg(reinterpret_cast<const float4*>(P.a.Cs + off + k0));
-          const float cs[4] = {c4.x, c4.y, c4.z, c4.w};
-          float c[4], s4[4];
-          cos_sin4(cs, &w[4 * m], c, s4);
-          // an invalid row contributes nothing
-          if (!valid) c[0] = c[1] = c[2] = c[3] = s4[0] = s4[1] = s4[2] = s4[3] = 0.f;
-          *reinterpret_cast<float4*>(buf + k0) = make_float4(c[0], c[1], c[2], c[3]);
-          *reinterpret_cast<float4*>(buf + d + k0) = make_float4(s4[0], s4[1], s4[2], s4[3]);
-        }
+        produce_row_1024<false>(P, n, valid, e, lane, buf);
         named_arrive(kBarFull + bsel, kTileThreads);
       }
     }
@@ -807,6 +859,300 @@ cudaError_t run_logits_tile(const Launch& P, const float* b, float* logits, cuda
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Fused logits at d = 1024 with the contraction W phi on the tensor cores.
+// Blocks of 16 warps own tiles of 12 rows. Warps 0..11 produce, in FP32 as in
+// k_logits_tile: warp w computes the 2048 features of row w of the tile (one
+// expansion per step) and writes each as fp16 hi = round(x), lo = round(x -
+// hi) into one of two shared 12-row buffers, already in the order of the
+// A operand of mma.m16n8k16 (mma_feat_word). Warps 12..15 contract the other
+// buffer with W_e: the buffer is the A operand (16 rows, rows 12..15 zero),
+// one 16-byte load per row and k-step; W is the B operand, split the same way
+// ahead of the launch (k_logits_wsplit) after scaling class c by a power of
+// two 2^s_c (exact), which keeps every class's weights inside fp16's range,
+// and streamed from L2 through a register ring kMmaPF k-steps ahead. Each
+// pair of k-steps forms the products lo.hi + hi.lo + hi.hi (the lo.lo term
+// is below 2^-22 of the product) in a fresh FP32 accumulator that is then
+// added to the running sum with a rounded FP32 add: the tensor core's own
+// accumulation truncates relative to the running value, which over hundreds
+// of steps into one accumulator left errors of 1e-4 on logits of a few
+// units. Consumer q covers k-steps [32 q, 32 q + 32) of the 128 16-feature
+// k-steps of an expansion, so its 16 x 16 accumulator tile sums over its
+// quarter of every expansion; the four are added in a fixed order per tile
+// and scaled back by 2^-s_c. Buffers change hands on the named barriers of
+// k_logits_tile.
+// ---------------------------------------------------------------------------
+constexpr int kMmaRows = 12;                     // producer warps = rows per tile
+constexpr int kMmaCons = 4;                      // consumer warps
+constexpr int kMmaThreads = (kMmaRows + kMmaCons) * 32;
+constexpr int kMmaRS = 2 * 1024 + 16;            // words per buffer row (= 16 mod 32, mma_feat_word)
+constexpr int kMmaKsteps = 2 * 1024 / 16;        // 16-feature k-steps per expansion
+constexpr int kMmaKsPerWarp = kMmaKsteps / kMmaCons;
+constexpr int kMmaPrefetchLines = 7;             // 12 x 7 >= 80 table lines per expansion
+// W fragment look-ahead in k-steps (a divisor of 8). Measured at 60000 rows,
+// E = 16, 10 classes: 2 steps 3.02 ms, 4 steps 2.98 ms, 8 steps 3.48 ms (the
+// ring no longer fits in registers).
+constexpr int kMmaPF = 4;
+
+int logits_mma_echunks(int64_t n, int E, int num_sms) {
+  const int64_t tiles = (n + kMmaRows - 1) / kMmaRows;
+  if (tiles >= num_sms) return 1;
+  const int64_t c = num_sms / tiles;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(c, E));
+}
+
+
+// B fragments of W (C x 2Ed) for the tensor-core logits. Block c fills class
+// slot c of the fragments (8 NT slots; zeros past C): with g = c % 8 and
+// nt = c / 8, lane 4 g + t of k-step ks of expansion e holds, as fp16 hi/lo
+// pairs, W_c at features 16 ks + 2 t, +1 (register b0) and 16 ks + 2 t + 8, +9
+// (b1) of the expansion, after scaling the class by 2^s_c with its largest
+// magnitude in [2^14, 2^15); inv[c] = 2^-s_c.
+template <int NT>
+__global__ void __launch_bounds__(256) k_logits_wsplit(const float* __restrict__ W, int C, int E,
+                                                       uint4* __restrict__ wf,
+                                                       float* __restrict__ inv) {
+  const int cls = blockIdx.x, g = cls & 7, nt = cls >> 3;
+  const int64_t F = 2ll * E * 1024;
+  const float* wr = W + (int64_t)cls * F;
+  const bool valid = cls < C;
+  __shared__ float wmax[8];
+  float m = 0.f;
+  if (valid)
+    for (int64_t k = threadIdx.x; k < F; k += blockDim.x) m = fmaxf(m, fabsf(__ldg(wr + k)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) m = fmaxf(m, wmax[i]);
+  int se = 0;  // scale exponent: m 2^se in [2^14, 2^15)
+  if (m > 0.f) se = min(max(14 - (((__float_as_int(m) >> 23) & 0xff) - 127), -100), 100);
+  const float scale = __int_as_float((se + 127) << 23);
+  if (threadIdx.x == 0 && valid) inv[cls] = __int_as_float((127 - se) << 23);
+  const int items = E * kMmaKsteps * 4;  // (expansion, k-step, t)
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int t = it & 3;
+    const int eks = it >> 2;  // e * kMmaKsteps + ks
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (valid) {
+      const int e = eks / kMmaKsteps, ks = eks % kMmaKsteps;
+      const float* q = wr + (int64_t)e * 2048 + 16 * ks + 2 * t;
+      split_f16(__ldg(q) * scale, __ldg(q + 1) * scale, v.x, v.z);
+      split_f16(__ldg(q + 8) * scale, __ldg(q + 9) * scale, v.y, v.w);
+    }
+    wf[((int64_t)eks * NT + nt) * 32 + g * 4 + t] = v;
+  }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(kMmaThreads, 1) k_logits_mma(const Launch P,
+                                                               const float* __restrict__ b,
+                                                               float* __restrict__ logits,
+                                                               int echunks) {
+  constexpr int d = 1024;
+  static_assert(Lay<10>::SLOT <= kMmaRS, "the row slice is the producer's slot");
+  static_assert(kMmaRows * kMmaPrefetchLines >= (d / 2 + 2 * d) / 32, "prefetch covers the tables");
+  extern __shared__ float4 sm4[];
+  float* phis = reinterpret_cast<float*>(sm4);  // [2][kMmaRows][kMmaRS]
+  float* red = phis + 2 * kMmaRows * kMmaRS;    // [kMmaCons][16 rows][16 classes]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int C = P.C, E = P.a.E;
+  const int64_t tiles = (P.a.n + kMmaRows - 1) / kMmaRows;
+  const int64_t units = tiles * echunks;
+  if (warp < kMmaRows) {
+    // ------------------------------ producers ------------------------------
+    int64_t step = 0;
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+      const int64_t tile = u / echunks;
+      const int ch = (int)(u % echunks);
+      const int e0 = E * ch / echunks, e1 = E * (ch + 1) / echunks;
+      const int64_t n = tile * kMmaRows + warp;
+      const bool valid = n < P.a.n;
+      for (int e = e0; e < e1; ++e, ++step) {
+        const int bsel = (int)(step & 1);
+        if (step >= 2) named_barrier(kBarEmpty + bsel, kMmaThreads);
+        float* buf = phis + (bsel * kMmaRows + warp) * kMmaRS;
+        {  // the next step's tables (permS, G, Cs: 80 lines of 128 B) into L1
+          const int64_t offn = (int64_t)(e + 1 < E ? e + 1 : 0) * d;
+          const int li = warp * kMmaPrefetchLines + lane;
+          if (lane < kMmaPrefetchLines && li < 80) {
+            const float* gsrc = P.a.GB ? P.a.GB : P.a.G;
+            const char* line =
+                li < 16   ? reinterpret_cast<const char*>(P.a.permS + offn / 2) + li * 128
+                : li < 48 ? reinterpret_cast<const char*>(gsrc + offn) + (li - 16) * 128
+                          : reinterpret_cast<const char*>(P.a.Cs + offn) + (li - 48) * 128;
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(line));
+          }
+        }
+        produce_row_1024<true>(P, n, valid, e, lane, buf);
+        named_arrive(kBarFull + bsel, kMmaThreads);
+      }
+    }
+    for (int64_t s = step < 2 ? 2 : step; s < step + 2; ++s)
+      named_barrier(kBarEmpty + (int)(s & 1), kMmaThreads);
+    return;
+  }
+  // ------------------------------- consumers -------------------------------
+  const int cw = warp - kMmaRows, ct = threadIdx.x - kMmaRows * 32;
+  const int g = lane >> 2, t = lane & 3;
+  const bool rows8 = g + 8 < kMmaRows;  // the lane's second row exists
+  // word of the lane's 4-word chunk in a k-step for rotations rho = 0..3
+  const int chunk0 = 4 * t, chunk1 = 4 * ((t + 1) & 3), chunk2 = 4 * ((t + 2) & 3),
+            chunk3 = 4 * ((t + 3) & 3);
+  bool wcls[NT];
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt) wcls[nt] = 8 * nt + g < C;  // the lane's class is real
+  // W fragments stream through a ring of kMmaPF k-steps in registers, each
+  // load issued kMmaPF steps before its use and across the ends of
+  // expansions and tiles, so its L2 latency is covered by the steps between.
+  auto wptr = [&](int e) {
+    return P.wf + ((int64_t)e * kMmaKsteps + cw * kMmaKsPerWarp) * NT * 32 + lane;
+  };
+  static_assert(8 % kMmaPF == 0 && kMmaKsPerWarp % 8 == 0, "whole rings per 8 k-steps");
+  uint4 ring[kMmaPF][NT];
+#pragma unroll
+  for (int j = 0; j < kMmaPF; ++j)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) ring[j][nt] = make_uint4(0u, 0u, 0u, 0u);
+  if (blockIdx.x < units) {
+    const uint4* w0 = wptr(E * (int)(blockIdx.x % echunks) / echunks);
+#pragma unroll
+    for (int j = 0; j < kMmaPF; ++j)
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt)
+        if (wcls[nt]) ring[j][nt] = __ldg(w0 + (j * NT + nt) * 32);
+  }
+  int64_t step = 0;
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int64_t tile = u / echunks;
+    const int ch = (int)(u % echunks);
+    const int e0 = E * ch / echunks, e1 = E * (ch + 1) / echunks;
+    float acc[NT][4];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+    for (int e = e0; e < e1; ++e, ++step) {
+      const int bsel = (int)(step & 1);
+      // row g (and g + 8) of the buffer at this warp's first k-step
+      const float* r0 = phis + bsel * kMmaRows * kMmaRS + g * kMmaRS + 16 * (cw * kMmaKsPerWarp);
+      // the expansion after this one in the warp's sequence, for the look-ahead
+      int en = e + 1;
+      if (en >= e1) {
+        const int64_t un = u + gridDim.x;
+        en = un < units ? E * (int)(un % echunks) / echunks : -1;
+      }
+      const uint4* wq = wptr(e);
+      const uint4* wqn = en >= 0 ? wptr(en) : nullptr;
+      named_barrier(kBarFull + bsel, kMmaThreads);
+      // One k-step: its W from the ring (the slot refilled from `src` when
+      // `more`), its A registers of rows g and g + 8 (zero past the tile's 12
+      // rows), and the products into the accumulator of its pair of k-steps,
+      // which the odd step adds to the running sum. Branch-free, so the
+      // compiler can interleave the independent chains of four pairs.
+      float pr[2][NT][4];
+      auto kstep = [&](const int i, const int j, const uint4* src, const bool more) {
+        uint4 wv[NT];
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          wv[nt] = ring[j % kMmaPF][nt];
+          if (more && wcls[nt]) ring[j % kMmaPF][nt] = __ldg(src + nt * 32);
+        }
+        const int rho = (j >> 1) & 3;
+        const float* q =
+            r0 + 16 * i + (rho == 0 ? chunk0 : rho == 1 ? chunk1 : rho == 2 ? chunk2 : chunk3);
+        const uint4 v = *reinterpret_cast<const uint4*>(q);
+        uint4 v8 = make_uint4(0u, 0u, 0u, 0u);
+        if (rows8) v8 = *reinterpret_cast<const uint4*>(q + 8 * kMmaRS);
+        const uint32_t ah[4] = {v.x, v8.x, v.z, v8.z};
+        const uint32_t al[4] = {v.y, v8.y, v.w, v8.w};
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          float (&a)[4] = pr[(j >> 1) & 1][nt];
+          if (j % 2 == 0) h16::mma16816_f16_zero(a, al, wv[nt].x, wv[nt].y);
+          else h16::mma16816_f16(a, al, wv[nt].x, wv[nt].y);
+          h16::mma16816_f16(a, ah, wv[nt].z, wv[nt].w);
+          h16::mma16816_f16(a, ah, wv[nt].x, wv[nt].y);
+          if (j % 2 == 1) {
+            const float2 s01 = add2(make_float2(acc[nt][0], acc[nt][1]), make_float2(a[0], a[1]));
+            const float2 s23 = add2(make_float2(acc[nt][2], acc[nt][3]), make_float2(a[2], a[3]));
+            acc[nt][0] = s01.x;
+            acc[nt][1] = s01.y;
+            acc[nt][2] = s23.x;
+            acc[nt][3] = s23.y;
+          }
+        }
+      };
+#pragma unroll 1
+      for (int i0 = 0; i0 < kMmaKsPerWarp - 8; i0 += 8) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) kstep(i0 + j, j, wq + (i0 + j + kMmaPF) * NT * 32, true);
+      }
+      // the last 8 steps: the look-ahead moves on to the next expansion
+      const uint4* wqs = wqn ? wqn : wq;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int i = kMmaKsPerWarp - 8 + j;
+        if (j + kMmaPF < 8) kstep(i, j, wq + (i + kMmaPF) * NT * 32, true);
+        else kstep(i, j, wqs + (j + kMmaPF - 8) * NT * 32, wqn != nullptr);
+      }
+      named_arrive(kBarEmpty + bsel, kMmaThreads);
+    }
+    // ---- the four k-quarters, added in a fixed order, scaled back ----
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      float* rq = red + (cw * 16) * 16 + 8 * nt + 2 * t;
+      rq[g * 16] = acc[nt][0];
+      rq[g * 16 + 1] = acc[nt][1];
+      rq[(g + 8) * 16] = acc[nt][2];
+      rq[(g + 8) * 16 + 1] = acc[nt][3];
+    }
+    named_barrier(kBarReduce, kMmaCons * 32);
+    for (int o = ct; o < kMmaRows * C; o += kMmaCons * 32) {
+      const int sr = o / C, cls = o % C;
+      float v = 0.f;
+#pragma unroll
+      for (int qw = 0; qw < kMmaCons; ++qw) v += red[(qw * 16 + sr) * 16 + cls];
+      v *= __ldg(P.winv + cls);
+      const int64_t row = tile * kMmaRows + sr;
+      if (row < P.a.n) {
+        if (echunks == 1) logits[row * C + cls] = v + (b ? b[cls] : 0.f);
+        else P.part[(row * echunks + ch) * C + cls] = v;
+      }
+    }
+    named_barrier(kBarReduce, kMmaCons * 32);  // red is free for the next tile
+  }
+}
+
+template <int NT>
+cudaError_t run_logits_mma(Launch P, const float* W, const float* b, float* scratch,
+                           float* logits, cudaStream_t s) {
+  const int E = P.a.E;
+  uint4* wf = reinterpret_cast<uint4*>(scratch);
+  float* inv = scratch + (int64_t)E * kMmaKsteps * NT * 32 * 4;
+  P.wf = wf;
+  P.winv = inv;
+  P.part = inv + CMAX;
+  k_logits_wsplit<NT><<<NT * 8, 256, 0, s>>>(W, P.C, E, wf, inv);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const size_t smem = sizeof(float) * (2 * kMmaRows * kMmaRS + kMmaCons * 16 * 16);
+  err = cudaFuncSetAttribute(k_logits_mma<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+  if (err != cudaSuccess) return err;
+  const int echunks = logits_mma_echunks(P.a.n, E, P.a.num_sms);
+  const int64_t units = (P.a.n + kMmaRows - 1) / kMmaRows * echunks;
+  const unsigned grid =
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)P.a.num_sms));
+  k_logits_mma<NT><<<grid, kMmaThreads, smem, s>>>(P, b, logits, echunks);
+  err = cudaGetLastError();
+  if (err != cudaSuccess || echunks == 1) return err;
+  const int64_t total = P.a.n * P.C;
+  k_logits_reduce<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(P.part, b, P.a.n, echunks, P.C,
+                                                                  logits);
+  return cudaGetLastError();
+}
+
 template <class K>
 int occ_blocks(K kernel, int threads, size_t smem) {
   int b = 0;
@@ -903,6 +1249,23 @@ int64_t logits_scratch_floats(int L, int64_t n, int E, int C, int num_sms) {
   if (L != 10) return n * E * C;
   const int ec = logits_echunks(n, E, num_sms);
   return ec > 1 ? n * ec * C : 0;
+}
+
+int64_t logits_mma_scratch_floats(int64_t n, int E, int C, int num_sms) {
+  const int NT = C > 8 ? 2 : 1;
+  const int ec = logits_mma_echunks(n, E, num_sms);
+  return (int64_t)E * kMmaKsteps * NT * 32 * 4 + CMAX + (ec > 1 ? n * ec * C : 0);
+}
+
+cudaError_t launch_logits_mma(const FeatureArgs& a, const float* W, const float* b, int C,
+                              float* scratch, float* logits, cudaStream_t s) {
+  if (a.n == 0) return cudaSuccess;
+  if (a.L != 10 || C < 1 || C > CMAX) return cudaErrorInvalidValue;
+  Launch P = make_launch(a);
+  P.W = W;
+  P.C = C;
+  return C > 8 ? run_logits_mma<2>(P, W, b, scratch, logits, s)
+               : run_logits_mma<1>(P, W, b, scratch, logits, s);
 }
 
 cudaError_t launch_logits(const FeatureArgs& a, const float* W, const float* b, int C,

@@ -117,6 +117,11 @@ cudaError_t launch_chunked_features(const FeatureArgs& a, bool vec_x, float* phi
 // At d = 1024 the tile kernel writes logits directly and `part` is unused.
 // Floats of partial logits launch_logits needs in `part` (0: none).
 int64_t logits_scratch_floats(int L, int64_t n, int E, int C, int num_sms);
+// Tensor-core fused logits at d = 1024 (fp16 hi/lo split contraction): the
+// floats of scratch it takes (W fragments, scales, partial logits).
+int64_t logits_mma_scratch_floats(int64_t n, int E, int C, int num_sms);
+cudaError_t launch_logits_mma(const FeatureArgs& a, const float* W, const float* b, int C,
+                              float* scratch, float* logits, cudaStream_t s);
 cudaError_t launch_logits(const FeatureArgs& a, const float* W, const float* b, int C,
                           float* part, float* logits, cudaStream_t s);
 

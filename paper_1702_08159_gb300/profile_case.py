@@ -3,10 +3,12 @@
     python -m paper_1702_08159_gb300.profile_case features --d 1024 --E 16 --rows 15000
     python -m paper_1702_08159_gb300.profile_case logits --d 1024 --E 16 --rows 8192 --classes 10
     python -m paper_1702_08159_gb300.profile_case features --d 16384 --E 4 --rows 2048 --gaussian
+    python -m paper_1702_08159_gb300.profile_case logits --d 1024 --E 16 --rows 8192 --prec fp16_split
 
 Inputs: MNIST-shaped rows (784 values, ~80% zeros, others U[0,1), padded to
 d) by default, or N(0,1) rows of length d (--gaussian); RBF plan with the
-given sigma and seed. The workload runs `--launches` times (default 3, the
+given sigma and seed; --prec selects mck_features_ex / mck_fused_logits_ex
+precisions (default fp32). The workload runs `--launches` times (default 3, the
 first a warm-up) with the plan's automatic launch shape, then the process
 synchronises and prints one line. Under ncu, `-k regex:<kernel> -s 1 -c 1`
 captures the second launch.
@@ -32,6 +34,7 @@ def main(argv=None):
     p.add_argument("--seed", type=int, default=42)
     p.add_argument("--gaussian", action="store_true")
     p.add_argument("--launches", type=int, default=3)
+    p.add_argument("--prec", default="fp32")
     a = p.parse_args(argv)
 
     import torch
@@ -45,15 +48,15 @@ def main(argv=None):
     if a.what == "features":
         out = torch.empty((a.rows, plan.num_features), device="cuda")
         for _ in range(a.launches):
-            mck.features(plan, x, out=out)
+            mck.features(plan, x, out=out, prec=a.prec)
     else:
         W, b = wl.logit_weights(a.classes, plan.num_features, seed=a.seed)
         Wd, bd = torch.from_numpy(W).cuda(), torch.from_numpy(b).cuda()
         out = torch.empty((a.rows, a.classes), device="cuda")
         for _ in range(a.launches):
-            mck.fused_logits(plan, x, Wd, bd, out=out)
+            mck.fused_logits(plan, x, Wd, bd, out=out, prec=a.prec)
     torch.cuda.synchronize()
-    print(f"profile_case {a.what} d={a.d} E={a.E} rows={a.rows}: ok ({float(out[0, :4].sum()):.6f})")
+    print(f"profile_case {a.what} d={a.d} E={a.E} rows={a.rows} prec={a.prec}: ok ({float(out[0, :4].sum()):.6f})")
     plan.close()
 
 

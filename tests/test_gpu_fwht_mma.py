@@ -11,7 +11,7 @@ model, one per form, not the accuracy target.
 
 The accuracy target for the 16-bit forms is a max abs error of 2e-3 on the
 orthonormal output (error relative to sqrt(d) rms(x), as measured here).
-FP16 unsplit and both hi + lo forms meet it (test_north_star_bar).
+FP16 unsplit and both hi + lo forms meet it (test_accuracy_target).
 BF16 unsplit does NOT meet it: rounding the input to 8 significant bits alone
 leaves 2^-9 relative error per element, about 1.1e-3 rms after the transform
 and ~5e-3 at the maximum over millions of outputs (1.2e-2 measured at
@@ -31,7 +31,7 @@ pytestmark = pytest.mark.gpu
 BOUND = {"bf16": 2.0 ** -6, "fp16": 2.0 ** -8, "bf16_split": 2.0 ** -14, "fp16_split": 2.0 ** -18}
 # The target's max abs error for the 16-bit forms; BF16 unsplit is excluded
 # because it cannot meet it (module docstring).
-NORTH_STAR_BAR = 2e-3
+TARGET_BAR = 2e-3
 MEETS_BAR = ("fp16", "bf16_split", "fp16_split")
 
 
@@ -102,7 +102,7 @@ def test_tensor_core_rejects_unsupported_shapes(mck, dev):
 
 @pytest.mark.parametrize("prec", MEETS_BAR)
 @pytest.mark.parametrize("L,n", [(10, 4096), (14, 256), (20, 4)])
-def test_north_star_bar(mck, dev, L, n, prec):
+def test_accuracy_target(mck, dev, L, n, prec):
     """The 2e-3 max abs error target on many outputs (2^22 at d = 1024 and
     2^14, 2^22 at 2^20) for the forms that meet it."""
     d = 1 << L
@@ -110,4 +110,4 @@ def test_north_star_bar(mck, dev, L, n, prec):
     t = torch.from_numpy(x).to(dev)
     mck.fwht_(t, prec)
     err = _rel_err(t.cpu().numpy(), x)
-    assert err <= NORTH_STAR_BAR, (d, prec, err)
+    assert err <= TARGET_BAR, (d, prec, err)
