@@ -608,7 +608,12 @@ int skew_bases(const uint32_t* pi, uint64_t seed, int iters, uint8_t* base, Dest
   return best;
 }
 
+// Annealing steps for the slots' lane bases. The FP32 feature kernel's slot
+// takes 5x more: measured at d = 1024, E = 16 (60000 rows), 20000 steps give
+// 1.511 ms per pass, 100000 steps 1.506 ms (400000: the same) for 33 ms more
+// plan time; the tensor-core kernel's slot keeps the shorter run.
 constexpr int kSkewIters = 20000;
+constexpr int kSkewItersFp32 = 100000;
 
 }  // namespace
 
@@ -644,7 +649,7 @@ mck_status_t build_skew_tables(mck_plan_s* p) {
         mPerm[(size_t)e * (d / 2) + ((size_t)(i >> 2) * 32 + lam) * 4 + (i & 3)] =
             pack(pe, mb, lam, i, min_, mlane, mreg);
     uint8_t base[32];
-    skew_bases(pe, seed, kSkewIters, base, [](int l, int j) { return Lay<10>::kB(l, j); },
+    skew_bases(pe, seed, kSkewItersFp32, base, [](int l, int j) { return Lay<10>::kB(l, j); },
                [](int src) { return lane_of(src); }, [](int src) { return reg_of(src); });
     for (int l = 0; l < 32; ++l) ubase[(size_t)e * 32 + l] = base[l];
     // Lane lam's 16 packed words: word i holds the byte offsets of its
