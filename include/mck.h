@@ -29,7 +29,12 @@
  *   learning C and G by backpropagation).
  * - `stream` is a cudaStream_t (NULL = the legacy default stream). Every
  *   compute call is asynchronous on that stream; the library may allocate
- *   stream-ordered scratch memory (cudaMallocAsync) on it.
+ *   stream-ordered scratch memory on it (cudaMallocFromPoolAsync from a
+ *   memory pool the library makes per device on first use, which keeps up
+ *   to 1 GiB mapped between calls so that a call after a synchronisation
+ *   does not map its scratch anew; the default pool is left untouched).
+ *   After a context reset (cudaDeviceReset) every later call is invalid, as
+ *   plans are.
  * - Gradients are written (not accumulated). Reductions over the batch (dCs,
  *   dG, dW, db) are deterministic: the same inputs give bit-identical outputs.
  * - Every call returns an mck_status_t. On failure mck_last_error() gives a

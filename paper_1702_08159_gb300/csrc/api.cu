@@ -174,6 +174,47 @@ mck_status_t launched(cudaError_t err, const char* where) {
   return err == cudaSuccess ? MCK_OK : cuda_fail(err, where);
 }
 
+// The memory pool of a device that the calls' scratch comes from. The
+// device's default pool hands unused memory back to the driver at every
+// synchronisation (release threshold 0), so a call made after a synchronise
+// would map its scratch anew each time; this pool keeps up to kScratchKeep
+// bytes mapped between calls. Made on first use, with the device current (a
+// process-wide setting of the default pool stays untouched); a context
+// reset invalidates it, as it does plans. Null if it cannot be made: the
+// scratch then comes from the default pool.
+constexpr uint64_t kScratchKeep = 1ull << 30;
+constexpr int kMaxDevices = 64;
+
+cudaMemPool_t scratch_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[kMaxDevices] = {};
+  static bool failed[kMaxDevices] = {};
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[device] && !failed[device]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    uint64_t keep = kScratchKeep;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess ||
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+      cudaGetLastError();
+      if (pool) cudaMemPoolDestroy(pool);
+      failed[device] = true;
+      return nullptr;
+    }
+    pools[device] = pool;
+  }
+  return pools[device];
+}
+
 // Stream-ordered scratch, freed on the same stream when the owner goes out of scope.
 struct Scratch {
   void* ptr = nullptr;
@@ -181,7 +222,10 @@ struct Scratch {
   explicit Scratch(cudaStream_t st) : s(st) {}
   mck_status_t alloc(size_t bytes) {
     if (bytes == 0) return MCK_OK;
-    if (cudaMallocAsync(&ptr, bytes, s) != cudaSuccess) {
+    cudaMemPool_t pool = scratch_pool();
+    const cudaError_t err = pool ? cudaMallocFromPoolAsync(&ptr, bytes, pool, s)
+                                 : cudaMallocAsync(&ptr, bytes, s);
+    if (err != cudaSuccess) {
       cudaGetLastError();
       ptr = nullptr;
       return fail(MCK_ENOMEM, "scratch allocation of " + std::to_string(bytes) + " bytes failed");
