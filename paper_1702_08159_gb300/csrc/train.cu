@@ -45,14 +45,17 @@ constexpr int kBwdInputMinBlocks = 8;  // k_bwd_input keeps dx in registers as w
 constexpr int CMAX = MCK_MAX_CLASSES;
 
 // ---------------------------------------------------------------------------
-// Softmax cross-entropy: one block, fixed-order sums (deterministic).
+// Softmax cross-entropy: one block; thread i takes rows i, i + 1024, ...; the
+// loss is summed in FP64 in a fixed order (lanes by a shuffle tree, then the
+// warps in order), so it is bit-reproducible.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_softmax_xent(const float* __restrict__ logits,
                                                        const int32_t* __restrict__ labels,
                                                        int64_t n, int C, float* __restrict__ loss,
                                                        float* __restrict__ dlogits) {
-  __shared__ double red[1024];
+  __shared__ double red[32];
   double acc = 0.0;
+  const float inv_n = n > 0 ? 1.0f / (float)n : 0.f;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
     const float* l = logits + i * C;
     const int y = labels[i];
@@ -64,20 +67,21 @@ __global__ void __launch_bounds__(1024) k_softmax_xent(const float* __restrict__
     const float lse = m + logf(s);
     if (ok) acc += (double)(lse - l[y]);
     if (dlogits) {
-      const float inv_n = 1.0f / (float)n;
       for (int c = 0; c < C; ++c) {
         const float p = expf(l[c] - lse);
         dlogits[i * C + c] = ok ? (p - (c == y ? 1.f : 0.f)) * inv_n : 0.f;
       }
     }
   }
-  red[threadIdx.x] = acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-    __syncthreads();
+  if (threadIdx.x == 0 && loss) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *loss = n > 0 ? (float)(t / (double)n) : 0.f;
   }
-  if (threadIdx.x == 0 && loss) *loss = n > 0 ? (float)(red[0] / (double)n) : 0.f;
 }
 
 // ---------------------------------------------------------------------------
