@@ -756,11 +756,15 @@ def configs01_leg(mck, dev, stream, args):
         pl = mck.Plan(D, E1, kern, 3.0, SEED, matern_t=40)
         ms = timed(lambda: mck.features(pl, x1, out=f1), max(3, args.steps // 5))
         ml = timed(lambda: mck.fused_logits(pl, x1, Wd, bd, out=lo), 3)
+        ref = lo.clone()
+        mt = timed(lambda: mck.fused_logits(pl, x1, Wd, bd, out=lo, prec="fp16_split"), 3)
         gbs = N * (IN_DIM * 4 + F1 * 4) / (ms / 1e3) / 1e9
         out[f"config1_{kern}"] = {"rows": N, "E": E1, "sigma": 3.0, "ms_features": ms,
                                   "features_per_s": N * F1 / (ms / 1e3), "gbs": gbs,
                                   "frac_of_measured_hbm": gbs / peak,
-                                  "ms_fused_logits": ml, "logit_rows_per_s": N / (ml / 1e3)}
+                                  "ms_fused_logits": ml, "logit_rows_per_s": N / (ml / 1e3),
+                                  "ms_fused_logits_tensor_core": mt,
+                                  "tensor_core_max_abs_diff": float((lo - ref).abs().max())}
         pl.close()
     del f1, x1
     # the headline at a power-of-2 batch (N = 2^16)

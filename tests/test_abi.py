@@ -71,6 +71,10 @@ def test_calls_reject_null_plan_and_arguments(lib):
                                      None) == -1
     assert lib.mck_fused_logits(None, v(16), 1, 1, 1, None, None, v(16), None, 10, v(16),
                                 None) == -1
+    for prec in (0, 4, 3):  # FP32, the tensor-core split, and an unbuilt contraction precision
+        assert lib.mck_fused_logits_ex(None, v(16), 1, 1, 1, None, None, v(16), None, 10, v(16),
+                                       prec, None) == -1
+        assert lib.mck_features_ex(None, v(16), 1, 1, 1, None, None, v(16), prec, None) == -1
     assert lib.mck_fwht(v(16), 1, 3, 0, None) == -1          # d not a power of two
     assert lib.mck_fwht(v(16), 1, 1 << 21, 0, None) == -5    # beyond 2^20
     assert lib.mck_fwht(v(16), 1, 8, 7, None) == -5          # unknown precision
