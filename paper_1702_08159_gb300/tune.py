@@ -14,6 +14,13 @@ Three tunables, each with bit-identical results for every setting:
 * tune_fwht: the regime of the FP32 transform at d = 2^16 and 2^17 (one pass
   on clusters of 2^15- or 2^14-float blocks, or two passes).
 
+and one choice between arithmetic forms held to the same accuracy bar:
+
+* tune_logits: the contraction of the fused logits at d = 1024 (FP32 FMAs or
+  the tensor-core fp16 hi/lo split). The two round differently, both within
+  the fused logits' 1e-4 bar against the FP64 oracle; the tuner returns the
+  faster precision for fused_logits(..., prec=...) and sets nothing.
+
 The tuner times each candidate on the caller's own data with CUDA events and
 keeps the fastest; results are cached in a JSON file keyed by the workload's
 signature (sizes and the GPU name), so a sweep runs once per workload shape.
@@ -153,6 +160,36 @@ def tune_fwht(x, regimes=FWHT_REGIMES, reps=5, cache=None):
     best = min(times, key=times.get)
     if cache:
         _write_cache(cache, key, {"kind": "fwht", "regime": best, "ms": times})
+    return best, times, False
+
+
+LOGIT_PRECISIONS = ("fp32", "fp16_split")
+
+
+def tune_logits(plan, x, W, b=None, precs=LOGIT_PRECISIONS, reps=5, cache=None):
+    """The faster contraction of fused_logits for inputs like x and weights
+    like W; returns (prec, {prec: ms}, from_cache). Below or above d = 1024
+    only the FP32 contraction exists and is returned untimed."""
+    from . import fused_logits
+
+    if plan.d != 1024:
+        return "fp32", {}, False
+    cache = _cache_path(cache)
+    n = x.shape[0]
+    nb = 1 << max(0, int(n - 1).bit_length())
+    h = hashlib.sha256(f"logits:{plan.d}:{plan.E}:{nb}:{x.shape[1]}:{W.shape[0]}".encode())
+    h.update(torch.cuda.get_device_name(plan.device).encode())
+    key = h.hexdigest()[:24]
+    if cache:
+        entry = _read_cache(cache).get(key)
+        if entry and entry.get("kind") == "logits":
+            return entry["prec"], dict(entry["ms"]), True
+    out = torch.empty((n, W.shape[0]), device=x.device)
+    times = {p: _events_ms(lambda: fused_logits(plan, x, W, b, out=out, prec=p), reps, x.device)
+             for p in precs}
+    best = min(times, key=times.get)
+    if cache:
+        _write_cache(cache, key, {"kind": "logits", "prec": best, "ms": times})
     return best, times, False
 
 

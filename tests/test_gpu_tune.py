@@ -104,3 +104,26 @@ def test_transform_regimes_agree(mck, dev, L, tmp_path):
     assert cached2 and r2 == r
     with pytest.raises(mck.MckError, match="INVAL"):
         mck.fwht_(torch.zeros((1, 1024), device=dev), "fp32", "two_pass")
+
+
+def test_logit_contraction_tuner(mck, dev, tmp_path):
+    """tune_logits times both contractions (each held to the fused logits'
+    1e-4 bar against the oracle by tests/test_gpu_logits_mma.py), returns the
+    faster one, and reuses its cache; at d != 1024 only FP32 exists."""
+    cache = str(tmp_path / "tl.json")
+    plan = mck.Plan(1024, 4, "rbf", 3.0, 42)
+    x = torch.from_numpy(wl.mnist_like(3000, 784, seed=4)).to(dev)
+    W = torch.from_numpy(wl.logit_weights(10, plan.num_features, seed=4)[0]).to(dev)
+    prec, times, cached = tune.tune_logits(plan, x, W, reps=2, cache=cache)
+    assert not cached and set(times) == set(tune.LOGIT_PRECISIONS) and prec in times
+    assert times[prec] == min(times.values())
+    prec2, times2, cached2 = tune.tune_logits(plan, x, W, reps=2, cache=cache)
+    assert cached2 and prec2 == prec and set(times2) == set(times)
+    a = mck.fused_logits(plan, x, W, prec=prec)
+    b = mck.fused_logits(plan, x, W)
+    assert (a - b).abs().max().item() <= 1e-4
+    plan.close()
+    p2 = mck.Plan(512, 2, "rbf", 3.0, 1)
+    W2 = torch.zeros((10, p2.num_features), device=dev)
+    assert tune.tune_logits(p2, torch.zeros((4, 512), device=dev), W2, cache=cache) == ("fp32", {}, False)
+    p2.close()
