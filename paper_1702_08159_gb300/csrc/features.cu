@@ -230,7 +230,13 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_FEATURES ? kWarpMinB
   // Row-wise output stores at d = 32 and 64 (feature sweep: 0.746 -> 0.337 ms
   // and 0.409 -> 0.381 ms); at d = 128 the staging cost more than it saved.
   constexpr bool kRows = MODE == MODE_FEATURES && L <= 6;
-  constexpr int kBuf = kRows && kRowsBuf > WS::VPW * Y::SLOT ? kRowsBuf : WS::VPW * Y::SLOT;
+  // At d = 32 a lane holds a whole vector and the slot serves only u and the
+  // Pi gather (the layout moves are identities there): an odd stride puts the
+  // 32 vectors' slots on 32 distinct banks for both the stores and the gather
+  // (every vector of the warp gathers the same positions), instead of 4-way
+  // conflicts with the padded stride.
+  constexpr int kSlot = L == 5 ? 33 : Y::SLOT;
+  constexpr int kBuf = kRows && kRowsBuf > WS::VPW * kSlot ? kRowsBuf : WS::VPW * kSlot;
   __shared__ __align__(16) float sm[kWarps][kBuf];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane / Y::T, lam = lane % Y::T;
@@ -272,7 +278,7 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_FEATURES ? kWarpMinB
       const int64_t off = (int64_t)e * d;
       // Lane-ordered tables: entry (m, lam, q) holds element kB(lam, 4m+q).
       bmask = __ldg(P.a.maskA + (int64_t)e * Y::T + lam);
-      const uint32_t slot = buf_addr + 4u * (uint32_t)(g * Y::SLOT);
+      const uint32_t slot = buf_addr + 4u * (uint32_t)(g * kSlot);
       // Gather offsets are below 2^16 bytes: two per register.
       pslot = slot;
       if constexpr (L == 10) {  // skewed slot, offsets packed at plan time
@@ -340,8 +346,15 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_FEATURES ? kWarpMinB
       }
       hreg<Y::maskB()>(w);
       // v = Pi u: u goes to shared memory, each register gathers its source.
-      if constexpr (L == 10) store_skew(buf, ubase, w);
-      else store_B<L>(buf, g, lam, w);
+      if constexpr (L == 10) {
+        store_skew(buf, ubase, w);
+      } else if constexpr (L == 5) {
+        float* q = buf + g * kSlot;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) q[j] = w[j];
+      } else {
+        store_B<L>(buf, g, lam, w);
+      }
       __syncwarp();
 #pragma unroll
       for (int j = 0; j < 32; ++j)
