@@ -141,6 +141,13 @@ __global__ void __launch_bounds__(1 << (L - 5)) k_fwht_chunks(float* __restrict_
       store_B<10>(buf, 0, lane, w);
     }
     __syncthreads();
+    // At 2^15 (one block per SM) this block's next vector goes into L2 while
+    // the current one is transformed: 0.381 -> 0.355 ms per GiB; at 2^11..2^14
+    // several blocks share an SM and the prefetch only competed for HBM
+    // (0.351 -> 0.373 ms), so it is left out there.
+    if constexpr (L == 15)
+      if (v + gridDim.x < n && lane == 0)
+        prefetch_l2_bulk(row + ((int64_t)gridDim.x << L) + warp * 1024, 4096u);
 #pragma unroll
     for (int j = 0; j < CPT; ++j) {
       const int c = threadIdx.x + NT * j;
@@ -231,6 +238,12 @@ __global__ void __launch_bounds__(1 << (LS - 5)) k_fwht_cluster(float* __restric
       store_B<10>(buf, 0, lane, w);
     }
     __syncthreads();
+    // The cluster's next vector: this warp's chunk of it into L2 while the
+    // current one is transformed and exchanged (issued after this vector's
+    // loads, so as not to compete with them): 2^16 0.531 -> 0.490 ms, 2^17
+    // 0.614 -> 0.579 ms.
+    if (v + ncl < n && lane == 0)
+      prefetch_l2_bulk(row + ncl * (int64_t)(S * CS) + (int64_t)r * S + warp * 1024, 4096u);
     // index bits 10..LS-1: across the slice's chunks, in place
 #pragma unroll
     for (int j = 0; j < CPT; ++j) {
