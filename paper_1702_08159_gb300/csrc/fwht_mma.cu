@@ -29,6 +29,7 @@
 
 #include <algorithm>
 
+#include "common.cuh"
 #include "internal.h"
 #include "mma_h16.cuh"
 
@@ -111,6 +112,11 @@ __global__ void __launch_bounds__(1 << (L - 5)) k_fwht_mma_cta(float* __restrict
         }
     }
     __syncthreads();
+    // At 2^15 (one block per SM) the block's next vector goes into L2 while this
+    // one is transformed, as in the FP32 block transform.
+    if constexpr (L == 15)
+      if (vec + gridDim.x < n && lane == 0)
+        prefetch_l2_bulk(row + ((int64_t)gridDim.x << L) + warp * 1024, 4096u);
 #pragma unroll
     for (int j = 0; j < CPT; ++j) {
       const int c = threadIdx.x + NT * j;
