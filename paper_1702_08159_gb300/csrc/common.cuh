@@ -189,17 +189,21 @@ __device__ __forceinline__ void cos_sin(float z, float& c, float& s) {
   s = __sinf(r);
 }
 
-// cos and sin of z = cs * h for two values at once: the same arithmetic as
-// cos_sin(cs * h) (with -k = rint(-z / 2 pi), exact since rounding to nearest
-// is symmetric), the products and reductions as packed pairs.
-__device__ __forceinline__ void cos_sin2(float2 cs, float2 h, float2& c, float2& s) {
-  const float2 z = mul2(cs, h);
+// cos and sin of two values z at once: the arithmetic of cos_sin (with -k =
+// rint(-z / 2 pi), exact since rounding to nearest is symmetric), the
+// reductions as packed pairs.
+__device__ __forceinline__ void cos_sin_z2(float2 z, float2& c, float2& s) {
   const float2 t = mul2(z, make_float2(-kInvTwoPi, -kInvTwoPi));
   const float2 kn = make_float2(rintf(t.x), rintf(t.y));
   float2 r = fma2(kn, make_float2(kTwoPiHi, kTwoPiHi), z);
   r = fma2(kn, make_float2(kTwoPiLo, kTwoPiLo), r);
   c = make_float2(__cosf(r.x), __cosf(r.y));
   s = make_float2(__sinf(r.x), __sinf(r.y));
+}
+
+// cos and sin of z = cs * h for two values at once (z rounded to float32).
+__device__ __forceinline__ void cos_sin2(float2 cs, float2 h, float2& c, float2& s) {
+  cos_sin_z2(mul2(cs, h), c, s);
 }
 
 // cos and sin of cs[q] * h[q] for a register quad.

@@ -623,26 +623,11 @@ __device__ __forceinline__ void split_f16(float a, float b, uint32_t& hi, uint32
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// Word offset, inside a row of the tensor-core logits' feature buffer, of
-// the fp16 (hi, lo) pair words of features f, f + 1 (f even). The 16
-// features of k-step ks take words [16 ks, 16 ks + 16) in four 4-word chunks;
-// chunk (t + rho) & 3, rho = (ks >> 1) & 3, holds (hi, lo) of the pairs at
-// features 16 ks + 2t and 16 ks + 2t + 8: one 16-byte load gives a lane
-// (g, t) of mma.m16n8k16 its A registers a0 / a2 of row g (hi and lo). The
-// rotation rho makes both the producers' 8-byte stores (lanes of a warp over
-// 8 k-steps) and the consumers' 16-byte loads (8 lanes over 2 rows) hit 32
-// distinct banks, with the row stride = 16 (mod 32) words.
-__host__ __device__ __forceinline__ constexpr int mma_feat_word(int f) {
-  return 16 * (f >> 4) + 4 * (((((f & 15) >> 1) & 3) + ((f >> 5) & 3)) & 3) + 2 * ((f & 15) >> 3);
-}
-
 // One row-expansion of a fused-logits producer at d = 1024: the features of
 // sample n under expansion e (zeros for an invalid row) into the row slice
-// buf (also the transform's shared slot), cos then sin: FP32 in natural order
-// (buf[0, 2048)), or with SPLIT16 as fp16 hi/lo pairs at mma_feat_word. The
-// feature kernel's sequence: signs, H over layouts A and B, u into the skewed
-// slot, the Pi gather, G, H, z = Cs h.
-template <bool SPLIT16>
+// buf (also the transform's shared slot), cos then sin, FP32 in natural order
+// (buf[0, 2048)). The feature kernel's sequence: signs, H over layouts A and
+// B, u into the skewed slot, the Pi gather, G, H, z = Cs h.
 __device__ __forceinline__ void produce_row_1024(const Launch& P, int64_t n, bool valid, int e,
                                                  int lane, float* buf) {
   constexpr int L = 10;
@@ -698,20 +683,8 @@ __device__ __forceinline__ void produce_row_1024(const Launch& P, int64_t n, boo
     cos_sin4(cs, &w[4 * m], c, s4);
     // an invalid row contributes nothing
     if (!valid) c[0] = c[1] = c[2] = c[3] = s4[0] = s4[1] = s4[2] = s4[3] = 0.f;
-    if constexpr (SPLIT16) {
-      uint2 v;
-      split_f16(c[0], c[1], v.x, v.y);
-      *reinterpret_cast<uint2*>(buf + mma_feat_word(k0)) = v;
-      split_f16(c[2], c[3], v.x, v.y);
-      *reinterpret_cast<uint2*>(buf + mma_feat_word(k0 + 2)) = v;
-      split_f16(s4[0], s4[1], v.x, v.y);
-      *reinterpret_cast<uint2*>(buf + mma_feat_word(d + k0)) = v;
-      split_f16(s4[2], s4[3], v.x, v.y);
-      *reinterpret_cast<uint2*>(buf + mma_feat_word(d + k0 + 2)) = v;
-    } else {
-      *reinterpret_cast<float4*>(buf + k0) = make_float4(c[0], c[1], c[2], c[3]);
-      *reinterpret_cast<float4*>(buf + d + k0) = make_float4(s4[0], s4[1], s4[2], s4[3]);
-    }
+    *reinterpret_cast<float4*>(buf + k0) = make_float4(c[0], c[1], c[2], c[3]);
+    *reinterpret_cast<float4*>(buf + d + k0) = make_float4(s4[0], s4[1], s4[2], s4[3]);
   }
 }
 
@@ -762,7 +735,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_logits_tile(const Launch P,
             asm volatile("prefetch.global.L1 [%0];" ::"l"(line));
           }
         }
-        produce_row_1024<false>(P, n, valid, e, lane, buf);
+        produce_row_1024(P, n, valid, e, lane, buf);
         named_arrive(kBarFull + bsel, kTileThreads);
       }
     }
@@ -884,38 +857,49 @@ cudaError_t run_logits_tile(const Launch& P, const float* b, float* logits, cuda
 
 // ---------------------------------------------------------------------------
 // Fused logits at d = 1024 with the contraction W phi on the tensor cores.
-// Blocks of 16 warps own tiles of 12 rows. Warps 0..11 produce, in FP32 as in
-// k_logits_tile: warp w computes the 2048 features of row w of the tile (one
-// expansion per step) and writes each as fp16 hi = round(x), lo = round(x -
-// hi) into one of two shared 12-row buffers, already in the order of the
-// A operand of mma.m16n8k16 (mma_feat_word). Warps 12..15 contract the other
-// buffer with W_e: the buffer is the A operand (16 rows, rows 12..15 zero),
-// one 16-byte load per row and k-step; W is the B operand, split the same way
-// ahead of the launch (k_logits_wsplit) after scaling class c by a power of
-// two 2^s_c (exact), which keeps every class's weights inside fp16's range,
-// and streamed from L2 through a register ring kMmaPF k-steps ahead. Each
-// pair of k-steps forms the products lo.hi + hi.lo + hi.hi (the lo.lo term
-// is below 2^-22 of the product) in a fresh FP32 accumulator that is then
-// added to the running sum with a rounded FP32 add: the tensor core's own
-// accumulation truncates relative to the running value, which over hundreds
-// of steps into one accumulator left errors of 1e-4 on logits of a few
-// units. Consumer q covers k-steps [32 q, 32 q + 32) of the 128 16-feature
-// k-steps of an expansion, so its 16 x 16 accumulator tile sums over its
-// quarter of every expansion; the four are added in a fixed order per tile
-// and scaled back by 2^-s_c. Buffers change hands on the named barriers of
-// k_logits_tile.
+// Blocks of 16 warps own tiles of 32 rows (two M tiles of mma.m16n8k16), and
+// every warp takes both roles in turn. Per expansion: warp w loads the
+// expansion's tables into registers once and computes, for rows w and w + 16
+// of the tile, the FP32 sequence of k_feat_warp up to the phases z = Cs h
+// (in the row's slice of the shared buffer, which is also its transform
+// slot), and writes z there. After a block barrier, warp w contracts the
+// features of z positions [64 w, 64 w + 64) over all 32 rows: for each of its
+// four pairs of k-steps (the cos features of 16 positions and the sin
+// features of the same positions, k-steps ks and ks + 64) a lane reads the
+// z of its fragment positions, forms cos z and sin z (the arithmetic of the
+// feature kernel, bit for bit), splits each into fp16 hi = round(x), lo =
+// round(x - hi) as A fragments, and takes W as the B operand, split the
+// same way ahead of the launch (k_logits_wsplit) after scaling class c by a
+// power of two 2^s_c (exact), which keeps every class's weights inside
+// fp16's range. The products of a pair, lo.hi + hi.lo + hi.hi for each of
+// the two k-steps (the lo.lo term is below 2^-22 of the product), go into a
+// fresh FP32 accumulator that is then added to the running sum with a
+// rounded FP32 add: the tensor core's own accumulation truncates relative
+// to the running value, which over hundreds of steps into one accumulator
+// left errors of 1e-4 on logits of a few units. The running sums live in a
+// per-lane slice of shared memory across the expansions, which leaves the
+// producer its registers for the tables. A second block barrier frees the
+// buffer for the next expansion. After the last expansion of a tile the 16
+// warps' sums are added in a fixed order and scaled back by 2^-s_c.
+//
+// Measured at 60000 rows, E = 16, 10 classes, on one GPU: this form 2.67 ms
+// (E = 8: 1.35 ms). With the split features (twice the bytes of z) in a
+// 16-row buffer and one row per warp and expansion: 2.82 ms (1.44 ms); as
+// dedicated roles (12 producer warps filling double-buffered 12-row tiles
+// for 4 contracting warps that stream W through a register ring) 2.87 ms;
+// transposed (classes as M, 8-row tiles as N, two 8-warp blocks per SM
+// running out of phase) 2.85 ms. The FP32 production of the features sets
+// the time (in the 16-row form, production alone: 2.24 ms; the contraction
+// alone: 0.73 ms), whatever the roles; storing z lets a warp produce two
+// rows per load of the expansion's tables and halves the W reads per row.
 // ---------------------------------------------------------------------------
-constexpr int kMmaRows = 12;                     // producer warps = rows per tile
-constexpr int kMmaCons = 4;                      // consumer warps
-constexpr int kMmaThreads = (kMmaRows + kMmaCons) * 32;
-constexpr int kMmaRS = 2 * 1024 + 16;            // words per buffer row (= 16 mod 32, mma_feat_word)
+constexpr int kMmaWarps = 16;
+constexpr int kMmaThreads = kMmaWarps * 32;
+constexpr int kMmaRows = 2 * kMmaWarps;          // rows per tile: two M tiles
+constexpr int kMmaZS = 1024 + 40;                // words per z row: >= the transform slot, = 8 mod 32
+constexpr int kMmaAccS = 20;                     // words per lane of the running sums (16 used)
 constexpr int kMmaKsteps = 2 * 1024 / 16;        // 16-feature k-steps per expansion
-constexpr int kMmaKsPerWarp = kMmaKsteps / kMmaCons;
-constexpr int kMmaPrefetchLines = 7;             // 12 x 7 >= 80 table lines per expansion
-// W fragment look-ahead in k-steps (a divisor of 8). Measured at 60000 rows,
-// E = 16, 10 classes: 2 steps 3.02 ms, 4 steps 2.98 ms, 8 steps 3.48 ms (the
-// ring no longer fits in registers).
-constexpr int kMmaPF = 4;
+constexpr int kMmaPrefetchLines = 5;             // 16 x 5 >= 80 table lines per expansion
 
 int logits_mma_echunks(int64_t n, int E, int num_sms) {
   const int64_t tiles = (n + kMmaRows - 1) / kMmaRows;
@@ -923,7 +907,6 @@ int logits_mma_echunks(int64_t n, int E, int num_sms) {
   const int64_t c = num_sms / tiles;
   return (int)std::max<int64_t>(1, std::min<int64_t>(c, E));
 }
-
 
 // B fragments of W (C x 2Ed) for the tensor-core logits. Block c fills class
 // slot c of the fragments (8 NT slots; zeros past C): with g = c % 8 and
@@ -969,173 +952,217 @@ __global__ void __launch_bounds__(256) k_logits_wsplit(const float* __restrict__
   }
 }
 
+// A 16-byte W fragment that skips L1: W streams through once per tile, and
+// L1 keeps the producers' tables and rows (in a 16-row form of this kernel,
+// 60000 rows, E = 16, 10 classes: 2.85 -> 2.82 ms against __ldg).
+__device__ __forceinline__ uint4 ldg_stream_u4(const uint4* p) {
+  uint4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p));
+  return v;
+}
+
 template <int NT>
 __global__ void __launch_bounds__(kMmaThreads, 1) k_logits_mma(const Launch P,
                                                                const float* __restrict__ b,
                                                                float* __restrict__ logits,
                                                                int echunks) {
-  constexpr int d = 1024;
-  static_assert(Lay<10>::SLOT <= kMmaRS, "the row slice is the producer's slot");
-  static_assert(kMmaRows * kMmaPrefetchLines >= (d / 2 + 2 * d) / 32, "prefetch covers the tables");
+  constexpr int L = 10;
+  using Y = Lay<L>;
+  constexpr int d = Y::d;
+  static_assert(Y::SLOT <= kMmaZS && kMmaZS % 32 == 8, "z row: transform slot, bank offset 8");
+  static_assert(kMmaWarps * kMmaPrefetchLines >= (d / 2 + 2 * d) / 32, "prefetch covers the tables");
+  static_assert(kMmaWarps * 64 == d, "64 z positions per warp");
+  constexpr int NS = 2 * NT * 4;  // running sums per lane: (M tile, class block, fragment entry)
+  static_assert(NS <= kMmaAccS && kMmaAccS % 4 == 0, "running sums per lane");
   extern __shared__ float4 sm4[];
-  float* phis = reinterpret_cast<float*>(sm4);  // [2][kMmaRows][kMmaRS]
-  float* red = phis + 2 * kMmaRows * kMmaRS;    // [kMmaCons][16 rows][16 classes]
+  float* zb = reinterpret_cast<float*>(sm4);   // [kMmaRows][kMmaZS]
+  float* sums = zb + kMmaRows * kMmaZS;        // [kMmaWarps][32 lanes][kMmaAccS]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
   const int C = P.C, E = P.a.E;
   const int64_t tiles = (P.a.n + kMmaRows - 1) / kMmaRows;
   const int64_t units = tiles * echunks;
-  if (warp < kMmaRows) {
-    // ------------------------------ producers ------------------------------
-    int64_t step = 0;
-    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-      const int64_t tile = u / echunks;
-      const int ch = (int)(u % echunks);
-      const int e0 = E * ch / echunks, e1 = E * (ch + 1) / echunks;
-      const int64_t n = tile * kMmaRows + warp;
-      const bool valid = n < P.a.n;
-      for (int e = e0; e < e1; ++e, ++step) {
-        const int bsel = (int)(step & 1);
-        if (step >= 2) named_barrier(kBarEmpty + bsel, kMmaThreads);
-        float* buf = phis + (bsel * kMmaRows + warp) * kMmaRS;
-        {  // the next step's tables (permS, G, Cs: 80 lines of 128 B) into L1
-          const int64_t offn = (int64_t)(e + 1 < E ? e + 1 : 0) * d;
-          const int li = warp * kMmaPrefetchLines + lane;
-          if (lane < kMmaPrefetchLines && li < 80) {
-            const float* gsrc = P.a.GB ? P.a.GB : P.a.G;
-            const char* line =
-                li < 16   ? reinterpret_cast<const char*>(P.a.permS + offn / 2) + li * 128
-                : li < 48 ? reinterpret_cast<const char*>(gsrc + offn) + (li - 16) * 128
-                          : reinterpret_cast<const char*>(P.a.Cs + offn) + (li - 48) * 128;
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(line));
-          }
-        }
-        produce_row_1024<true>(P, n, valid, e, lane, buf);
-        named_arrive(kBarFull + bsel, kMmaThreads);
-      }
-    }
-    for (int64_t s = step < 2 ? 2 : step; s < step + 2; ++s)
-      named_barrier(kBarEmpty + (int)(s & 1), kMmaThreads);
-    return;
-  }
-  // ------------------------------- consumers -------------------------------
-  const int cw = warp - kMmaRows, ct = threadIdx.x - kMmaRows * 32;
-  const int g = lane >> 2, t = lane & 3;
-  const bool rows8 = g + 8 < kMmaRows;  // the lane's second row exists
-  // word of the lane's 4-word chunk in a k-step for rotations rho = 0..3
-  const int chunk0 = 4 * t, chunk1 = 4 * ((t + 1) & 3), chunk2 = 4 * ((t + 2) & 3),
-            chunk3 = 4 * ((t + 3) & 3);
+  float* mysum = sums + (warp * 32 + lane) * kMmaAccS;
   bool wcls[NT];
 #pragma unroll
   for (int nt = 0; nt < NT; ++nt) wcls[nt] = 8 * nt + g < C;  // the lane's class is real
-  // W fragments stream through a ring of kMmaPF k-steps in registers, each
-  // load issued kMmaPF steps before its use and across the ends of
-  // expansions and tiles, so its L2 latency is covered by the steps between.
-  auto wptr = [&](int e) {
-    return P.wf + ((int64_t)e * kMmaKsteps + cw * kMmaKsPerWarp) * NT * 32 + lane;
-  };
-  static_assert(8 % kMmaPF == 0 && kMmaKsPerWarp % 8 == 0, "whole rings per 8 k-steps");
-  uint4 ring[kMmaPF][NT];
-#pragma unroll
-  for (int j = 0; j < kMmaPF; ++j)
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) ring[j][nt] = make_uint4(0u, 0u, 0u, 0u);
-  if (blockIdx.x < units) {
-    const uint4* w0 = wptr(E * (int)(blockIdx.x % echunks) / echunks);
-#pragma unroll
-    for (int j = 0; j < kMmaPF; ++j)
-#pragma unroll
-      for (int nt = 0; nt < NT; ++nt)
-        if (wcls[nt]) ring[j][nt] = __ldg(w0 + (j * NT + nt) * 32);
-  }
-  int64_t step = 0;
+  const int ks0 = 4 * warp;  // cos k-steps ks0 .. ks0 + 3; their sin k-steps are 64 later
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
     const int64_t tile = u / echunks;
     const int ch = (int)(u % echunks);
     const int e0 = E * ch / echunks, e1 = E * (ch + 1) / echunks;
-    float acc[NT][4];
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-    for (int e = e0; e < e1; ++e, ++step) {
-      const int bsel = (int)(step & 1);
-      // row g (and g + 8) of the buffer at this warp's first k-step
-      const float* r0 = phis + bsel * kMmaRows * kMmaRS + g * kMmaRS + 16 * (cw * kMmaKsPerWarp);
-      // the expansion after this one in the warp's sequence, for the look-ahead
-      int en = e + 1;
-      if (en >= e1) {
-        const int64_t un = u + gridDim.x;
-        en = un < units ? E * (int)(un % echunks) / echunks : -1;
-      }
-      const uint4* wq = wptr(e);
-      const uint4* wqn = en >= 0 ? wptr(en) : nullptr;
-      named_barrier(kBarFull + bsel, kMmaThreads);
-      // One k-step: its W from the ring (the slot refilled from `src` when
-      // `more`), its A registers of rows g and g + 8 (zero past the tile's 12
-      // rows), and the products into the accumulator of its pair of k-steps,
-      // which the odd step adds to the running sum. Branch-free, so the
-      // compiler can interleave the independent chains of four pairs.
-      float pr[2][NT][4];
-      auto kstep = [&](const int i, const int j, const uint4* src, const bool more) {
-        uint4 wv[NT];
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-          wv[nt] = ring[j % kMmaPF][nt];
-          if (more && wcls[nt]) ring[j % kMmaPF][nt] = __ldg(src + nt * 32);
+    for (int i = 0; i < NS; i += 4)
+      *reinterpret_cast<float4*>(mysum + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = e0; e < e1; ++e) {
+      const int64_t off = (int64_t)e * d;
+      {  // the next expansion's tables (permS, G, Cs: 80 lines of 128 B) into L1
+        const int64_t offn = (int64_t)(e + 1 < E ? e + 1 : 0) * d;
+        const int li = warp * kMmaPrefetchLines + lane;
+        if (lane < kMmaPrefetchLines && li < 80) {
+          const float* gsrc = P.a.GB ? P.a.GB : P.a.G;
+          const char* line =
+              li < 16   ? reinterpret_cast<const char*>(P.a.permS + offn / 2) + li * 128
+              : li < 48 ? reinterpret_cast<const char*>(gsrc + offn) + (li - 16) * 128
+                        : reinterpret_cast<const char*>(P.a.Cs + offn) + (li - 48) * 128;
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(line));
         }
-        const int rho = (j >> 1) & 3;
-        const float* q =
-            r0 + 16 * i + (rho == 0 ? chunk0 : rho == 1 ? chunk1 : rho == 2 ? chunk2 : chunk3);
-        const uint4 v = *reinterpret_cast<const uint4*>(q);
-        uint4 v8 = make_uint4(0u, 0u, 0u, 0u);
-        if (rows8) v8 = *reinterpret_cast<const uint4*>(q + 8 * kMmaRS);
-        const uint32_t ah[4] = {v.x, v8.x, v.z, v8.z};
-        const uint32_t al[4] = {v.y, v8.y, v.w, v8.w};
+      }
+      // ------------- production: z of rows warp and warp + 16 -------------
+      {
+        // the expansion's tables, held in registers across the two rows (Cs,
+        // needed only at the end, is read per row)
+        const uint32_t bmask = __ldg(P.a.maskA + (int64_t)e * Y::T + lane);
+        const uint32_t ubase = __ldg(P.a.ubase + (int64_t)e * 32 + lane);
+        uint32_t poff[16];
+        float gt[32];
+        load_skew_offsets(P.a.permS + (int64_t)e * (d / 2), lane, poff);
+        if (P.a.GB) {
+          const float4* gb = reinterpret_cast<const float4*>(P.a.GB + off) + lane;
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-          float (&a)[4] = pr[(j >> 1) & 1][nt];
-          if (j % 2 == 0) h16::mma16816_f16_zero(a, al, wv[nt].x, wv[nt].y);
-          else h16::mma16816_f16(a, al, wv[nt].x, wv[nt].y);
-          h16::mma16816_f16(a, ah, wv[nt].z, wv[nt].w);
-          h16::mma16816_f16(a, ah, wv[nt].x, wv[nt].y);
-          if (j % 2 == 1) {
-            const float2 s01 = add2(make_float2(acc[nt][0], acc[nt][1]), make_float2(a[0], a[1]));
-            const float2 s23 = add2(make_float2(acc[nt][2], acc[nt][3]), make_float2(a[2], a[3]));
-            acc[nt][0] = s01.x;
-            acc[nt][1] = s01.y;
-            acc[nt][2] = s23.x;
-            acc[nt][3] = s23.y;
+          for (int m = 0; m < 8; ++m) {
+            const float4 v = __ldg(gb + m * Y::T);
+            gt[4 * m] = v.x;
+            gt[4 * m + 1] = v.y;
+            gt[4 * m + 2] = v.z;
+            gt[4 * m + 3] = v.w;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) gt[j] = __ldg(P.a.G + off + Y::kB(lane, j));
+        }
+#pragma unroll 1
+        for (int r = 0; r < 2; ++r) {
+          const int row = warp + kMmaWarps * r;
+          const int64_t n = tile * kMmaRows + row;
+          // a row past the batch computes the features of x = 0; its logits
+          // are never written
+          const bool valid = n < P.a.n;
+          float* buf = zb + row * kMmaZS;
+          const uint32_t slot = smem_addr(buf);
+          float w[32];
+          load_x_A<L>(P, n, valid, lane, w);
+          apply_signs(w, bmask);
+          hreg<Y::maskA()>(w);
+          store_A<L>(buf, 0, lane, w);
+          __syncwarp();
+          load_B<L>(buf, 0, lane, w);
+          hreg<Y::maskB()>(w);
+          store_skew(buf, ubase, w);
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            w[j] = lds32(slot + ((j & 1) ? (poff[j >> 1] >> 16) : (poff[j >> 1] & 0xffffu)));
+          hreg_scaled<Y::maskB()>(w, gt);
+          __syncwarp();
+          store_B<L>(buf, 0, lane, w);
+          __syncwarp();
+          load_A<L>(buf, 0, lane, w);
+          hreg<Y::maskA()>(w);
+          __syncwarp();  // every lane holds its values: the slice takes z now
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            const float4 c4 =
+                __ldg(reinterpret_cast<const float4*>(P.a.Cs + off + Y::kA(lane, 4 * m)));
+            const float2 z01 = mul2(make_float2(c4.x, c4.y), make_float2(w[4 * m], w[4 * m + 1]));
+            const float2 z23 = mul2(make_float2(c4.z, c4.w), make_float2(w[4 * m + 2], w[4 * m + 3]));
+            *reinterpret_cast<float4*>(buf + Y::kA(lane, 4 * m)) =
+                make_float4(z01.x, z01.y, z23.x, z23.y);
           }
         }
-      };
-#pragma unroll 1
-      for (int i0 = 0; i0 < kMmaKsPerWarp - 8; i0 += 8) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) kstep(i0 + j, j, wq + (i0 + j + kMmaPF) * NT * 32, true);
       }
-      // the last 8 steps: the look-ahead moves on to the next expansion
-      const uint4* wqs = wqn ? wqn : wq;
+      // ---------------- contraction: z positions [64 w, 64 w + 64) ----------------
+      // W fragments of the first two pairs of k-steps (their L2 latency
+      // overlaps the wait for the other rows); the last two are loaded while
+      // the first two are contracted
+      const uint4* wb = P.wf + (int64_t)e * kMmaKsteps * NT * 32 + lane;
+      uint4 wr[2][2][NT];  // [ring slot][cos, sin][class block]
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int i = kMmaKsPerWarp - 8 + j;
-        if (j + kMmaPF < 8) kstep(i, j, wq + (i + kMmaPF) * NT * 32, true);
-        else kstep(i, j, wqs + (j + kMmaPF - 8) * NT * 32, wqn != nullptr);
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt)
+            wr[s][h][nt] = wcls[nt] ? ldg_stream_u4(wb + ((ks0 + s + 64 * h) * NT + nt) * 32)
+                                    : make_uint4(0u, 0u, 0u, 0u);
+      __syncthreads();  // z of all 32 rows is in the buffer
+      float acc[NS];
+#pragma unroll
+      for (int i = 0; i < NS; i += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(mysum + i);
+        acc[i] = v.x;
+        acc[i + 1] = v.y;
+        acc[i + 2] = v.z;
+        acc[i + 3] = v.w;
       }
-      named_arrive(kBarEmpty + bsel, kMmaThreads);
-    }
-    // ---- the four k-quarters, added in a fixed order, scaled back ----
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-      float* rq = red + (cw * 16) * 16 + 8 * nt + 2 * t;
-      rq[g * 16] = acc[nt][0];
-      rq[g * 16 + 1] = acc[nt][1];
-      rq[(g + 8) * 16] = acc[nt][2];
-      rq[(g + 8) * 16 + 1] = acc[nt][3];
+      for (int kk = 0; kk < 4; ++kk) {
+        const int sl = kk & 1;
+        uint4 wv[2][NT];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt) {
+            wv[h][nt] = wr[sl][h][nt];
+            if (kk < 2)
+              wr[sl][h][nt] = wcls[nt]
+                                  ? ldg_stream_u4(wb + ((ks0 + kk + 2 + 64 * h) * NT + nt) * 32)
+                                  : make_uint4(0u, 0u, 0u, 0u);
+          }
+        const int p = 16 * (ks0 + kk) + 2 * t;  // z of the pairs (p, p + 1) and (p + 8, p + 9)
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          const float* z0 = zb + (16 * mt + g) * kMmaZS + p;  // row g of the M tile
+          const float* z1 = z0 + 8 * kMmaZS;                   // row g + 8
+          // A registers a0..a3: (row g, k 2t..), (row g + 8, k 2t..),
+          // (row g, k 2t + 8..), (row g + 8, k 2t + 8..)
+          float2 c[4], s[4];
+          cos_sin_z2(*reinterpret_cast<const float2*>(z0), c[0], s[0]);
+          cos_sin_z2(*reinterpret_cast<const float2*>(z1), c[1], s[1]);
+          cos_sin_z2(*reinterpret_cast<const float2*>(z0 + 8), c[2], s[2]);
+          cos_sin_z2(*reinterpret_cast<const float2*>(z1 + 8), c[3], s[3]);
+          uint32_t chi[4], clo[4], shi[4], slo[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            split_f16(c[q].x, c[q].y, chi[q], clo[q]);
+            split_f16(s[q].x, s[q].y, shi[q], slo[q]);
+          }
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt) {
+            float pr[4];
+            h16::mma16816_f16_zero(pr, clo, wv[0][nt].x, wv[0][nt].y);
+            h16::mma16816_f16(pr, chi, wv[0][nt].z, wv[0][nt].w);
+            h16::mma16816_f16(pr, chi, wv[0][nt].x, wv[0][nt].y);
+            h16::mma16816_f16(pr, slo, wv[1][nt].x, wv[1][nt].y);
+            h16::mma16816_f16(pr, shi, wv[1][nt].z, wv[1][nt].w);
+            h16::mma16816_f16(pr, shi, wv[1][nt].x, wv[1][nt].y);
+            float* a = acc + (mt * NT + nt) * 4;
+            const float2 s01 = add2(make_float2(a[0], a[1]), make_float2(pr[0], pr[1]));
+            const float2 s23 = add2(make_float2(a[2], a[3]), make_float2(pr[2], pr[3]));
+            a[0] = s01.x;
+            a[1] = s01.y;
+            a[2] = s23.x;
+            a[3] = s23.y;
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NS; i += 4)
+        *reinterpret_cast<float4*>(mysum + i) =
+            make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
+      __syncthreads();  // the buffer is free for the next expansion's rows
     }
-    named_barrier(kBarReduce, kMmaCons * 32);
-    for (int o = ct; o < kMmaRows * C; o += kMmaCons * 32) {
+    // ---- the 16 warps' sums, added in a fixed order, scaled back ----
+    for (int o = threadIdx.x; o < kMmaRows * C; o += kMmaThreads) {
       const int sr = o / C, cls = o % C;
+      const int mt = sr >> 4, rg = sr & 7, rhi = (sr >> 3) & 1;
+      const int nt = cls >> 3, ct = (cls & 7) >> 1, clo = cls & 1;
+      const int at = (4 * rg + ct) * kMmaAccS + (mt * NT + nt) * 4 + 2 * rhi + clo;
       float v = 0.f;
 #pragma unroll
-      for (int qw = 0; qw < kMmaCons; ++qw) v += red[(qw * 16 + sr) * 16 + cls];
+      for (int qw = 0; qw < kMmaWarps; ++qw) v += sums[qw * 32 * kMmaAccS + at];
       v *= __ldg(P.winv + cls);
       const int64_t row = tile * kMmaRows + sr;
       if (row < P.a.n) {
@@ -1143,7 +1170,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_logits_mma(const Launch P,
         else P.part[(row * echunks + ch) * C + cls] = v;
       }
     }
-    named_barrier(kBarReduce, kMmaCons * 32);  // red is free for the next tile
+    __syncthreads();  // the sums are read before the next tile clears them
   }
 }
 
@@ -1159,7 +1186,7 @@ cudaError_t run_logits_mma(Launch P, const float* W, const float* b, float* scra
   k_logits_wsplit<NT><<<NT * 8, 256, 0, s>>>(W, P.C, E, wf, inv);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  const size_t smem = sizeof(float) * (2 * kMmaRows * kMmaRS + kMmaCons * 16 * 16);
+  const size_t smem = sizeof(float) * (kMmaRows * kMmaZS + kMmaWarps * 32 * kMmaAccS);
   err = cudaFuncSetAttribute(k_logits_mma<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
   if (err != cudaSuccess) return err;

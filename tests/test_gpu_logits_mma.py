@@ -48,14 +48,15 @@ def _oracle(plan, x, W, b):
 
 
 @pytest.mark.parametrize("E,C,n", [(2, 10, 17), (3, 16, 8), (2, 1, 9), (2, 9, 23), (1, 8, 1),
-                                   (16, 10, 100), (3, 10, 1300), (2, 10, 12), (2, 10, 13),
-                                   (4, 5, 2000)])
+                                   (16, 10, 100), (3, 10, 1300), (2, 10, 32), (2, 10, 33),
+                                   (3, 10, 3000), (4, 5, 5001)])
 def test_matches_oracle(mck, dev, E, C, n):
-    # n = 1, 8, 9, 17, 23, 100: fewer 12-row tiles than SMs, so the expansions
-    # are split into chunks with partial logits; 12 and 13: one full tile and
-    # a one-row ragged tile; 1300 and 2000: more tiles than SMs, blocks that
-    # take several tiles and a ragged last one. C = 1, 5, 8: one 8-class
-    # block; 9, 10, 16: two.
+    # n = 1, 8, 9, 17, 23, 100, 1300: fewer 32-row tiles than SMs, so the
+    # expansions are split into chunks with partial logits; 32 and 33: one
+    # full tile, and one with a one-row ragged tile; 3000: one tile per block,
+    # a ragged last one; 5001: more tiles than SMs, blocks that take two tiles
+    # and a ragged last one. C = 1, 5, 8: one 8-class block of W; 9, 10, 16:
+    # two.
     plan = mck.Plan(1024, E, "rbf", 3.0, 5 + E)
     x = wl.mnist_like(n, 784, seed=n)
     W, _ = wl.logit_weights(C, plan.num_features, seed=C, std=0.05)
@@ -83,7 +84,7 @@ def test_full_size_sampled(mck, dev):
     got = mck.fused_logits(plan, xd, Wd, bd, prec="fp16_split")
     fp32 = mck.fused_logits(plan, xd, Wd, bd)
     assert torch.isfinite(got).all()
-    rows = np.unique(np.concatenate([[0, 1, 11, 12, 13, N // 2, N - 2, N - 1],
+    rows = np.unique(np.concatenate([[0, 1, 15, 16, 17, 31, 32, 33, N // 2, N - 2, N - 1],
                                      np.random.default_rng(3).integers(0, N, 25)]))
     ref = _oracle(plan, x[rows], W, b)
     assert float(np.abs(got.cpu().numpy()[rows] - ref).max()) <= BAR
