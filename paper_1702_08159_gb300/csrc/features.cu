@@ -857,54 +857,63 @@ cudaError_t run_logits_tile(const Launch& P, const float* b, float* logits, cuda
 
 // ---------------------------------------------------------------------------
 // Fused logits at d = 1024 with the contraction W phi on the tensor cores.
-// Blocks of 16 warps own tiles of 32 rows (two M tiles of mma.m16n8k16), and
-// every warp takes both roles in turn. Per expansion: warp w loads the
-// expansion's tables into registers once and computes, for rows w and w + 16
-// of the tile, the FP32 sequence of k_feat_warp up to the phases z = Cs h
-// (in the row's slice of the shared buffer, which is also its transform
-// slot), and writes z there. After a block barrier, warp w contracts the
-// features of z positions [64 w, 64 w + 64) over all 32 rows: for each of its
-// four pairs of k-steps (the cos features of 16 positions and the sin
-// features of the same positions, k-steps ks and ks + 64) a lane reads the
-// z of its fragment positions, forms cos z and sin z (the arithmetic of the
-// feature kernel, bit for bit), splits each into fp16 hi = round(x), lo =
-// round(x - hi) as A fragments, and takes W as the B operand, split the
-// same way ahead of the launch (k_logits_wsplit) after scaling class c by a
-// power of two 2^s_c (exact), which keeps every class's weights inside
-// fp16's range. The products of a pair, lo.hi + hi.lo + hi.hi for each of
-// the two k-steps (the lo.lo term is below 2^-22 of the product), go into a
-// fresh FP32 accumulator that is then added to the running sum with a
-// rounded FP32 add: the tensor core's own accumulation truncates relative
-// to the running value, which over hundreds of steps into one accumulator
-// left errors of 1e-4 on logits of a few units. The running sums live in a
-// per-lane slice of shared memory across the expansions, which leaves the
-// producer its registers for the tables. A second block barrier frees the
-// buffer for the next expansion. After the last expansion of a tile the 16
-// warps' sums are added in a fixed order and scaled back by 2^-s_c.
+// Blocks of kMmaWarps warps own tiles of 16 rows (the M of mma.m16n8k16),
+// several blocks per SM, and every warp takes both roles in turn. Per
+// expansion: warp w loads the expansion's tables into registers once and
+// computes, for its rows w, w + kMmaWarps, ... of the tile, the FP32
+// sequence of k_feat_warp up to the phases z = Cs h (in the row's slice of
+// the shared buffer, which is also its transform slot), and writes z there.
+// After a block barrier, warp w contracts the features of its z positions
+// (1024 / kMmaWarps of them) over all 16 rows: for each pair of k-steps (the
+// cos features of 16 positions and the sin features of the same positions,
+// k-steps ks and ks + 64) a lane reads the z of its fragment positions,
+// forms cos z and sin z (the arithmetic of the feature kernel, bit for bit),
+// splits each into fp16 hi = round(x), lo = round(x - hi) as A fragments,
+// and takes W as the B operand, split the same way ahead of the launch
+// (k_logits_wsplit) after scaling class c by a power of two 2^s_c (exact),
+// which keeps every class's weights inside fp16's range. The products of a
+// pair, lo.hi + hi.lo + hi.hi for each of its two k-steps (the lo.lo term is
+// below 2^-22 of the product), go into a fresh FP32 accumulator that is then
+// added to the running sum with a rounded FP32 add: the tensor core's own
+// accumulation truncates relative to the running value, which over hundreds
+// of steps into one accumulator left errors of 1e-4 on logits of a few
+// units. The running sums live in a per-lane slice of shared memory across
+// the expansions, which leaves the producer its registers for the tables. A
+// second block barrier frees the buffer for the next expansion. After the
+// last expansion of a tile the warps' sums are added in a fixed order and
+// scaled back by 2^-s_c. The blocks of an SM drift out of phase, so one
+// block's contraction (its cos and sin on the special-function units, its
+// MMAs) overlaps another's production (FP32 butterflies, shared memory).
 //
-// Measured at 60000 rows, E = 16, 10 classes, on one GPU: this form 2.67 ms
-// (E = 8: 1.35 ms). With the split features (twice the bytes of z) in a
-// 16-row buffer and one row per warp and expansion: 2.82 ms (1.44 ms); as
-// dedicated roles (12 producer warps filling double-buffered 12-row tiles
-// for 4 contracting warps that stream W through a register ring) 2.87 ms;
-// transposed (classes as M, 8-row tiles as N, two 8-warp blocks per SM
-// running out of phase) 2.85 ms. The FP32 production of the features sets
-// the time (in the 16-row form, production alone: 2.24 ms; the contraction
-// alone: 0.73 ms), whatever the roles; storing z lets a warp produce two
-// rows per load of the expansion's tables and halves the W reads per row.
+// Measured at 60000 rows, E = 16, 10 classes, on one GPU: two 8-warp blocks
+// per SM 2.27 ms (E = 8: 1.16 ms). One 16-warp block per SM with 32-row
+// tiles: 2.67 ms (1.35 ms; production alone 1.76 ms, the contraction alone
+// 1.12 ms: the two phases of one block do not overlap). With the split
+// features (twice the bytes of z) in a 16-row buffer and one row per warp
+// and expansion: 2.82 ms (1.44 ms); as dedicated roles (12 producer warps
+// filling double-buffered 12-row tiles for 4 contracting warps that stream
+// W through a register ring) 2.87 ms; transposed (classes as M, 8-row tiles
+// as N, two 8-warp blocks per SM) 2.85 ms. Storing z rather than the
+// features halves the buffer, which lets a warp produce several rows per
+// load of the expansion's tables and leaves room for several blocks per SM.
 // ---------------------------------------------------------------------------
-constexpr int kMmaWarps = 16;
+constexpr int kMmaWarps = 8;
+constexpr int kMmaBlocksPerSM = 2;
 constexpr int kMmaThreads = kMmaWarps * 32;
-constexpr int kMmaRows = 2 * kMmaWarps;          // rows per tile: two M tiles
+constexpr int kMmaRows = 16;                     // rows per tile
+constexpr int kMmaRPW = kMmaRows / kMmaWarps;    // rows per warp and table load
+constexpr int kMmaMT = kMmaRows / 16;            // M tiles per tile
+constexpr int kMmaKP = 64 / kMmaWarps;           // (cos, sin) k-step pairs per warp
 constexpr int kMmaZS = 1024 + 40;                // words per z row: >= the transform slot, = 8 mod 32
-constexpr int kMmaAccS = 20;                     // words per lane of the running sums (16 used)
+constexpr int kMmaAccS = 4 * (2 * kMmaMT + 1);   // words per lane of the running sums (8 MT used)
 constexpr int kMmaKsteps = 2 * 1024 / 16;        // 16-feature k-steps per expansion
-constexpr int kMmaPrefetchLines = 5;             // 16 x 5 >= 80 table lines per expansion
+constexpr int kMmaPrefetchLines = 80 / kMmaWarps;  // the 80 table lines per expansion
 
 int logits_mma_echunks(int64_t n, int E, int num_sms) {
   const int64_t tiles = (n + kMmaRows - 1) / kMmaRows;
-  if (tiles >= num_sms) return 1;
-  const int64_t c = num_sms / tiles;
+  const int64_t slots = (int64_t)num_sms * kMmaBlocksPerSM;
+  if (tiles >= slots) return 1;
+  const int64_t c = slots / tiles;
   return (int)std::max<int64_t>(1, std::min<int64_t>(c, E));
 }
 
@@ -964,7 +973,7 @@ __device__ __forceinline__ uint4 ldg_stream_u4(const uint4* p) {
 }
 
 template <int NT>
-__global__ void __launch_bounds__(kMmaThreads, 1) k_logits_mma(const Launch P,
+__global__ void __launch_bounds__(kMmaThreads, kMmaBlocksPerSM) k_logits_mma(const Launch P,
                                                                const float* __restrict__ b,
                                                                float* __restrict__ logits,
                                                                int echunks) {
@@ -973,8 +982,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_logits_mma(const Launch P,
   constexpr int d = Y::d;
   static_assert(Y::SLOT <= kMmaZS && kMmaZS % 32 == 8, "z row: transform slot, bank offset 8");
   static_assert(kMmaWarps * kMmaPrefetchLines >= (d / 2 + 2 * d) / 32, "prefetch covers the tables");
-  static_assert(kMmaWarps * 64 == d, "64 z positions per warp");
-  constexpr int NS = 2 * NT * 4;  // running sums per lane: (M tile, class block, fragment entry)
+  static_assert(kMmaWarps * kMmaKP * 16 == d && kMmaKP % 2 == 0, "z positions per warp");
+  constexpr int NS = kMmaMT * NT * 4;  // running sums per lane: (M tile, class block, entry)
   static_assert(NS <= kMmaAccS && kMmaAccS % 4 == 0, "running sums per lane");
   extern __shared__ float4 sm4[];
   float* zb = reinterpret_cast<float*>(sm4);   // [kMmaRows][kMmaZS]
@@ -988,7 +997,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_logits_mma(const Launch P,
   bool wcls[NT];
 #pragma unroll
   for (int nt = 0; nt < NT; ++nt) wcls[nt] = 8 * nt + g < C;  // the lane's class is real
-  const int ks0 = 4 * warp;  // cos k-steps ks0 .. ks0 + 3; their sin k-steps are 64 later
+  const int ks0 = kMmaKP * warp;  // cos k-steps ks0 .. ks0 + KP - 1; their sin k-steps are 64 later
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
     const int64_t tile = u / echunks;
     const int ch = (int)(u % echunks);
@@ -1010,10 +1019,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_logits_mma(const Launch P,
           asm volatile("prefetch.global.L1 [%0];" ::"l"(line));
         }
       }
-      // ------------- production: z of rows warp and warp + 16 -------------
+      // --------- production: z of rows warp, warp + kMmaWarps, ... ---------
       {
-        // the expansion's tables, held in registers across the two rows (Cs,
-        // needed only at the end, is read per row)
+        // the expansion's tables, held in registers across the warp's rows
+        // (Cs, needed only at the end, is read per row)
         const uint32_t bmask = __ldg(P.a.maskA + (int64_t)e * Y::T + lane);
         const uint32_t ubase = __ldg(P.a.ubase + (int64_t)e * 32 + lane);
         uint32_t poff[16];
@@ -1034,7 +1043,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_logits_mma(const Launch P,
           for (int j = 0; j < 32; ++j) gt[j] = __ldg(P.a.G + off + Y::kB(lane, j));
         }
 #pragma unroll 1
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < kMmaRPW; ++r) {
           const int row = warp + kMmaWarps * r;
           const int64_t n = tile * kMmaRows + row;
           // a row past the batch computes the features of x = 0; its logits
@@ -1073,10 +1082,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_logits_mma(const Launch P,
           }
         }
       }
-      // ---------------- contraction: z positions [64 w, 64 w + 64) ----------------
+      // ------ contraction: z positions [16 KP w, 16 KP (w + 1)), KP = kMmaKP ------
       // W fragments of the first two pairs of k-steps (their L2 latency
-      // overlaps the wait for the other rows); the last two are loaded while
-      // the first two are contracted
+      // overlaps the wait for the other rows); each later pair is loaded two
+      // pairs ahead of its use
       const uint4* wb = P.wf + (int64_t)e * kMmaKsteps * NT * 32 + lane;
       uint4 wr[2][2][NT];  // [ring slot][cos, sin][class block]
 #pragma unroll
@@ -1087,7 +1096,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_logits_mma(const Launch P,
           for (int nt = 0; nt < NT; ++nt)
             wr[s][h][nt] = wcls[nt] ? ldg_stream_u4(wb + ((ks0 + s + 64 * h) * NT + nt) * 32)
                                     : make_uint4(0u, 0u, 0u, 0u);
-      __syncthreads();  // z of all 32 rows is in the buffer
+      __syncthreads();  // z of all the tile's rows is in the buffer
       float acc[NS];
 #pragma unroll
       for (int i = 0; i < NS; i += 4) {
@@ -1098,7 +1107,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_logits_mma(const Launch P,
         acc[i + 3] = v.w;
       }
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
+      for (int kk = 0; kk < kMmaKP; ++kk) {
         const int sl = kk & 1;
         uint4 wv[2][NT];
 #pragma unroll
@@ -1106,14 +1115,14 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_logits_mma(const Launch P,
 #pragma unroll
           for (int nt = 0; nt < NT; ++nt) {
             wv[h][nt] = wr[sl][h][nt];
-            if (kk < 2)
+            if (kk + 2 < kMmaKP)
               wr[sl][h][nt] = wcls[nt]
                                   ? ldg_stream_u4(wb + ((ks0 + kk + 2 + 64 * h) * NT + nt) * 32)
                                   : make_uint4(0u, 0u, 0u, 0u);
           }
         const int p = 16 * (ks0 + kk) + 2 * t;  // z of the pairs (p, p + 1) and (p + 8, p + 9)
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
+        for (int mt = 0; mt < kMmaMT; ++mt) {
           const float* z0 = zb + (16 * mt + g) * kMmaZS + p;  // row g of the M tile
           const float* z1 = z0 + 8 * kMmaZS;                   // row g + 8
           // A registers a0..a3: (row g, k 2t..), (row g + 8, k 2t..),
@@ -1154,10 +1163,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_logits_mma(const Launch P,
             make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
       __syncthreads();  // the buffer is free for the next expansion's rows
     }
-    // ---- the 16 warps' sums, added in a fixed order, scaled back ----
+    // ---- the warps' sums, added in a fixed order, scaled back ----
     for (int o = threadIdx.x; o < kMmaRows * C; o += kMmaThreads) {
       const int sr = o / C, cls = o % C;
-      const int mt = sr >> 4, rg = sr & 7, rhi = (sr >> 3) & 1;
+      const int mt = sr >> 4, rg = sr & 7, rhi = (sr >> 3) & 1;  // M tile, row g, row g + 8
       const int nt = cls >> 3, ct = (cls & 7) >> 1, clo = cls & 1;
       const int at = (4 * rg + ct) * kMmaAccS + (mt * NT + nt) * 4 + 2 * rhi + clo;
       float v = 0.f;
@@ -1190,10 +1199,13 @@ cudaError_t run_logits_mma(Launch P, const float* W, const float* b, float* scra
   err = cudaFuncSetAttribute(k_logits_mma<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
   if (err != cudaSuccess) return err;
+  int occ = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_logits_mma<NT>, kMmaThreads, smem);
+  if (err != cudaSuccess) return err;
   const int echunks = logits_mma_echunks(P.a.n, E, P.a.num_sms);
   const int64_t units = (P.a.n + kMmaRows - 1) / kMmaRows * echunks;
-  const unsigned grid =
-      (unsigned)std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)P.a.num_sms));
+  const int64_t slots = (int64_t)P.a.num_sms * std::max(1, std::min(occ, kMmaBlocksPerSM));
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min(units, slots));
   k_logits_mma<NT><<<grid, kMmaThreads, smem, s>>>(P, b, logits, echunks);
   err = cudaGetLastError();
   if (err != cudaSuccess || echunks == 1) return err;

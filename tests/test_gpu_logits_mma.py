@@ -49,14 +49,14 @@ def _oracle(plan, x, W, b):
 
 @pytest.mark.parametrize("E,C,n", [(2, 10, 17), (3, 16, 8), (2, 1, 9), (2, 9, 23), (1, 8, 1),
                                    (16, 10, 100), (3, 10, 1300), (2, 10, 32), (2, 10, 33),
-                                   (3, 10, 3000), (4, 5, 5001)])
+                                   (3, 10, 3000), (4, 5, 8001)])
 def test_matches_oracle(mck, dev, E, C, n):
-    # n = 1, 8, 9, 17, 23, 100, 1300: fewer 32-row tiles than SMs, so the
-    # expansions are split into chunks with partial logits; 32 and 33: one
-    # full tile, and one with a one-row ragged tile; 3000: one tile per block,
-    # a ragged last one; 5001: more tiles than SMs, blocks that take two tiles
-    # and a ragged last one. C = 1, 5, 8: one 8-class block of W; 9, 10, 16:
-    # two.
+    # n from 1 to 1300: fewer 16-row tiles than resident blocks, so the
+    # expansions are split into chunks with partial logits; 32 and 33: whole
+    # tiles, and a one-row ragged tile; 3000 and 8001: hundreds of tiles, the
+    # latter more than the resident blocks, so that blocks take two tiles;
+    # ragged last tiles throughout. C = 1, 5, 8: one 8-class block of W; 9,
+    # 10, 16: two.
     plan = mck.Plan(1024, E, "rbf", 3.0, 5 + E)
     x = wl.mnist_like(n, 784, seed=n)
     W, _ = wl.logit_weights(C, plan.num_features, seed=C, std=0.05)
