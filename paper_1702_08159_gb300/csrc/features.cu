@@ -885,9 +885,11 @@ cudaError_t run_logits_tile(const Launch& P, const float* b, float* logits, cuda
 // block's contraction (its cos and sin on the special-function units, its
 // MMAs) overlaps another's production (FP32 butterflies, shared memory).
 //
-// Measured at 60000 rows, E = 16, 10 classes, on one GPU: two 8-warp blocks
-// per SM 2.27 ms (E = 8: 1.16 ms). One 16-warp block per SM with 32-row
-// tiles: 2.67 ms (1.35 ms; production alone 1.76 ms, the contraction alone
+// Measured at 60000 rows, E = 16, 10 classes, on one GPU: three 4-warp
+// blocks per SM (four rows per warp and table load, up to 170 registers)
+// 2.24 ms (E = 8: 1.14 ms); two 8-warp blocks 2.27 ms (1.16 ms), the same
+// with Cs also held across the rows (it spills) 2.33 ms. One 16-warp block
+// per SM with 32-row tiles: 2.67 ms (1.35 ms; production alone 1.76 ms, the contraction alone
 // 1.12 ms: the two phases of one block do not overlap). With the split
 // features (twice the bytes of z) in a 16-row buffer and one row per warp
 // and expansion: 2.82 ms (1.44 ms); as dedicated roles (12 producer warps
@@ -897,8 +899,8 @@ cudaError_t run_logits_tile(const Launch& P, const float* b, float* logits, cuda
 // features halves the buffer, which lets a warp produce several rows per
 // load of the expansion's tables and leaves room for several blocks per SM.
 // ---------------------------------------------------------------------------
-constexpr int kMmaWarps = 8;
-constexpr int kMmaBlocksPerSM = 2;
+constexpr int kMmaWarps = 4;
+constexpr int kMmaBlocksPerSM = 3;
 constexpr int kMmaThreads = kMmaWarps * 32;
 constexpr int kMmaRows = 16;                     // rows per tile
 constexpr int kMmaRPW = kMmaRows / kMmaWarps;    // rows per warp and table load
