@@ -302,8 +302,8 @@ mck_status_t mck_fused_logits(mck_plan_t plan, const float* x, int64_t n, int64_
  *         the tests hold the logits to the FP32 path's bar of 1e-4 against
  *         the FP64 oracle. Other precisions return MCK_EUNSUPPORTED.
  * Takes stream-ordered scratch for the split weights (E x 64 KiB, x 2 above
- * 8 classes) and, for batches with fewer 12-row tiles than SMs, n x
- * (expansion chunks) x num_classes partial logits. Other arguments, results
+ * 8 classes) and, for batches with fewer 16-row tiles than resident blocks
+ * (three per SM), n x (expansion chunks) x num_classes partial logits. Other arguments, results
  * and errors as mck_fused_logits. */
 mck_status_t mck_fused_logits_ex(mck_plan_t plan, const float* x, int64_t n, int64_t in_dim,
                                  int64_t ldx, const float* Cs, const float* G, const float* W,
