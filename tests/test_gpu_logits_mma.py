@@ -11,7 +11,7 @@ error grows like sqrt(K) 2^-22 rms|phi W|, about 1e-6 at the 60000 x E = 16
 MNIST-shaped workload with W ~ N(0, 0.05) (a bf16 split would leave about
 2.5e-5 rms there and miss the bar at the maximum over 600000 logits). The
 FP32 accumulation adds rounding of the running sums, ~2^-24 |sum| per add
-over K / 128 adds per consumer (each two 16-feature steps' products go into
+over K / 128 adds per warp (each two 16-feature steps' products go into
 a fresh tensor-core accumulator first: the tensor core's own accumulation
 truncates relative to the running value, and accumulating every step into one
 accumulator measured 1.6e-5 at E = 2 and 1.7e-4 at E = 16): a few 1e-6, below
@@ -142,6 +142,20 @@ def test_zero_class_and_learned_tables(mck, dev):
                     b.astype(np.float64))
     assert float(np.abs(got - ref).max()) <= BAR
     assert np.all(got[:, 4] == b[4])
+
+
+def test_strided_unaligned_rows(mck, dev):
+    """x as a strided view whose rows are 781 floats long (not a multiple of 4:
+    the producers' scalar loads) at a stride of 800, over three 16-row tiles,
+    the last ragged."""
+    plan = mck.Plan(1024, 2, "rbf", 3.0, 13)
+    n, in_dim, ld = 37, 781, 800
+    base = torch.from_numpy(wl.mnist_like(n, ld, seed=13)).to(dev)
+    x = base[:, :in_dim]
+    W, _ = wl.logit_weights(10, plan.num_features, seed=13, std=0.05)
+    got = mck.fused_logits(plan, x, torch.from_numpy(W).to(dev), prec="fp16_split")
+    ref = _oracle(plan, x.cpu().numpy(), W, np.zeros(10, np.float32))
+    assert float(np.abs(got.cpu().numpy() - ref).max()) <= BAR
 
 
 def test_deterministic(mck, dev):
